@@ -1,0 +1,89 @@
+"""Pins of the oracle's step definitions (filter, CholQR2, Rayleigh-Ritz, angles)."""
+import math
+
+import numpy as np
+import pytest
+
+from tests.conftest import crandn, rand_herm
+
+
+def test_filter_closed_form_on_diagonal(orc):
+    # for diagonal C the filter is the scalar polynomial p(lambda_j) on each row
+    from oracle import pieces
+    lam = np.linspace(-2, 50, 30)
+    Cm = np.diag(lam).astype(np.complex128)
+    rng = np.random.default_rng(11)
+    Y0 = crandn(rng, 30, 5)
+    lo, hi, s = 3.0, 50.0, -2.0
+    for d in (1, 2, 7, 16):
+        Y = pieces.chebyshev_filter(Cm, Y0, d, lo, hi, s)
+        p = pieces.cheb_scalar(d, lam, lo, hi, s)
+        assert np.allclose(Y, p[:, None] * Y0, rtol=1e-12, atol=1e-12)
+    # p(s) = 1 by construction and |p| <= 1/|T_d((s-c)/e)| on [lo, hi]
+    assert pieces.cheb_scalar(9, np.array([s]), lo, hi, s)[0] == pytest.approx(1.0)
+    inside = np.linspace(lo, hi, 101)
+    c, e = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    bound = 1.0 / abs(pieces.cheb_T(9, np.array([(s - c) / e]))[0])
+    assert np.abs(pieces.cheb_scalar(9, inside, lo, hi, s)).max() <= bound * (1 + 1e-12)
+
+
+def test_cheb_T_closed_form():
+    from oracle import pieces
+    x = np.array([-1.7, -1.0, -0.3, 0.0, 0.6, 1.0, 2.5])
+    # T_3(x) = 4x^3 - 3x, T_4(x) = 8x^4 - 8x^2 + 1
+    assert np.allclose(pieces.cheb_T(3, x), 4 * x**3 - 3 * x, rtol=1e-13, atol=1e-13)
+    assert np.allclose(pieces.cheb_T(4, x), 8 * x**4 - 8 * x**2 + 1, rtol=1e-13, atol=1e-13)
+
+
+def test_cholqr2_is_the_unique_qr(orc):
+    from oracle import pieces
+    rng = np.random.default_rng(12)
+    Y = crandn(rng, 200, 17) @ np.diag(np.logspace(0, 4, 17))
+    Q, R = pieces.cholqr2(Y)
+    assert np.abs(Q.conj().T @ Q - np.eye(17)).max() < 1e-13
+    assert np.abs(Q @ R - Y).max() < 1e-12 * np.abs(Y).max()
+    Qn, Rn = np.linalg.qr(Y)
+    ph = np.diag(Rn) / np.abs(np.diag(Rn))
+    Qn, Rn = Qn * ph, (Rn.T * ph.conj()).T
+    assert np.abs(Q - Qn).max() < 1e-10
+    assert np.allclose(np.triu(R), R)
+
+
+def test_rayleigh_ritz_exact_subspace(orc):
+    from oracle import pieces
+    rng = np.random.default_rng(13)
+    n, k = 60, 6
+    lam = np.sort(rng.uniform(-1, 10, n))
+    Qf, _ = np.linalg.qr(crandn(rng, n, n))
+    Cm = (Qf * lam) @ Qf.conj().T
+    Cm = 0.5 * (Cm + Cm.conj().T)
+    # a rotated basis of the invariant subspace of eigenvalues 2..7
+    Z, _ = np.linalg.qr(crandn(rng, k, k))
+    Q = Qf[:, 2:2 + k] @ Z
+    th, Qn, W = pieces.rayleigh_ritz(Cm, Q)
+    assert np.abs(th - lam[2:2 + k]).max() < 1e-12
+    assert pieces.residual_norms(W, Qn, th).max() < 1e-12
+
+
+def test_deviation_angles_known_rotation():
+    from oracle import pieces
+    n = 10
+    B = np.eye(n, dtype=np.complex128)
+    X0 = np.eye(n, dtype=np.complex128)[:, :2]
+    t = 0.3
+    X1 = X0.copy()
+    X1[:, 0] = math.cos(t) * X0[:, 0] + math.sin(t) * np.eye(n)[:, 5]
+    ang = pieces.deviation_angles(X0, X1, B)
+    assert ang[0] == pytest.approx(t / (math.pi / 2), rel=1e-12)
+    assert ang[1] == pytest.approx(0.0, abs=1e-7)
+
+
+def test_principal_sines_B_inner_product(orc):
+    from oracle import pieces
+    rng = np.random.default_rng(14)
+    n = 30
+    from tests.conftest import rand_hpd
+    B = rand_hpd(rng, n, 50)
+    X = crandn(rng, n, 3)
+    s = pieces.principal_sines(X, X @ crandn(rng, 3, 3), B)
+    assert s.max() < 1e-7
