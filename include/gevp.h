@@ -1,0 +1,182 @@
+/*
+ * gevp.h -- C ABI of libgevp: sequences of dense complex Hermitian-definite generalized
+ * eigenproblems A x = lambda B x on one GB300 (sm_103a).
+ *
+ * The problem is the one the paper poses for every k-point of every self-consistent
+ * outer iteration of an FLAPW DFT cycle (Sec. "Introduction to Density Functional
+ * Theory", Eq. 3 and the paragraph after it): A (the Hamiltonian) Hermitian, B (the
+ * overlap) Hermitian positive definite, the lowest nev eigenpairs wanted. The paper's
+ * Sec. "A new computational philosophy" treats the iterations as a sequence of
+ * correlated problems and seeds an iterative eigensolver with the previous problem's
+ * eigenvectors; its conclusions name an improved subspace iteration as the solver to
+ * build. This library does that: Cholesky reduction C = L^-1 A L^-H, then Chebyshev-
+ * filtered subspace iteration (CholQR2 orthonormalisation, Rayleigh-Ritz, residual
+ * locking) seeded with the previous eigenvectors.
+ *
+ * Conventions (all functions):
+ *  - Matrices are ROW-MAJOR, interleaved complex128 (C99 double complex / torch
+ *    complex128, 16 bytes per element), with a leading dimension ld >= number of columns.
+ *    A Hermitian matrix read column-major is its conjugate; the layout is fixed here.
+ *  - A and B are read in full (both triangles); they must be Hermitian. Results are
+ *    undefined if they are not.
+ *  - Every matrix/vector argument is DEVICE memory owned by the caller unless the
+ *    function name ends in _host. The library never frees caller memory.
+ *  - All work is enqueued on the handle's stream. A function returns after the work is
+ *    complete unless stated otherwise (the solver reads small status words back).
+ *  - Functions never abort or trap; they return a gevp_status. gevp_last_error() gives
+ *    a one-line message for the last failure on a handle.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Workspace belongs to the handle, is sized lazily, grows and is released by
+ *    gevp_destroy.
+ */
+#ifndef GEVP_H
+#define GEVP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gevp_ctx* gevp_handle;
+
+typedef enum {
+  GEVP_OK = 0,
+  GEVP_ERR_INVALID_ARG = 1,     /* a size, pointer or leading dimension is invalid   */
+  GEVP_ERR_NOT_HPD = 2,         /* B (or a Gram matrix) is not positive definite     */
+  GEVP_ERR_NO_CONVERGENCE = 3,  /* iteration cap hit; best results are still written */
+  GEVP_ERR_CUDA = 4,            /* a CUDA runtime call failed                        */
+  GEVP_ERR_OOM = 5,             /* device workspace could not be allocated           */
+  GEVP_ERR_TIMEOUT = 6,         /* a bounded device-side wait ran out                */
+  GEVP_ERR_INVALID_VALUE = 7,   /* NaN or Inf found in an input matrix               */
+  GEVP_ERR_UNSUPPORTED = 8      /* requested mode not available on this device       */
+} gevp_status;
+
+/* Precision of the Chebyshev filter (everything else is FP64). */
+typedef enum {
+  GEVP_PREC_FP64 = 0,   /* FP64 complex GEMM                                           */
+  GEVP_PREC_FP32 = 1,   /* FP32-class: split-BF16 (hi+lo) planar operands on tcgen05    */
+  GEVP_PREC_BF16 = 2    /* BF16 planar operands, 3-product (Gauss) complex GEMM on      */
+                        /* tcgen05 tensor cores, FP32 accumulation in TMEM              */
+} gevp_prec;
+
+typedef struct {
+  int filter_prec;      /* gevp_prec the filter starts in; switches to FP64 on stall    */
+  double tol;           /* target max_i ||A x_i - l_i B x_i|| / (||A|| ||x_i||); 1e-10  */
+  int max_outer;        /* cap on outer (filter + Rayleigh-Ritz) iterations per problem */
+  int deg_min, deg_max; /* Chebyshev degree range                                       */
+  int nex;              /* guard vectors (at least 2 are used); m = min(n, nev + nex)  */
+  uint64_t seed;        /* seed of the counter-based generator for random start blocks  */
+  int b_fixed;          /* 1: every problem of the sequence has the same B              */
+  int cold_start;       /* 1: every problem starts from a random block (no warm start)  */
+  int lanczos_steps;    /* steps of the Lanczos bound estimator                         */
+  int refine_iters;     /* refinement steps of the small eigensolver (>= 1)             */
+  int keep_all_X;       /* 1: X receives every problem's eigenvectors (nprob*n*nev)     */
+} gevp_opts;
+
+/* Per-problem counters and CUDA-event phase times (milliseconds). */
+typedef struct {
+  int outer_iters;      /* filter + orthonormalisation + Rayleigh-Ritz rounds           */
+  int filter_steps;     /* Chebyshev matrix-block products                              */
+  int switches;         /* filter precision switches to FP64                            */
+  int orth_fallbacks;   /* shifted CholQR fallbacks                                     */
+  int final_passes;     /* original-space residual checks                               */
+  int converged;        /* 1 if every residual <= tol                                   */
+  int64_t matvecs;      /* filter column-products (sum of active columns x degree)      */
+  double flops_fp64;    /* executed-flop model, FP64 work                               */
+  double flops_lowp;    /* executed-flop model, tensor-core filter work (complex, 8/MAC) */
+  double max_resid;
+  float ms_chol, ms_reduce, ms_bounds, ms_filter, ms_orth, ms_rr, ms_resid, ms_final, ms_total;
+} gevp_stats;
+
+/* Fills *o with the defaults: FP64 filter, tol 1e-10, max_outer 60, degrees 4..24,
+ * nex 0 (callers set it), seed 10074400, b_fixed 0, cold_start 0, lanczos_steps 32,
+ * refine_iters 2, keep_all_X 0. */
+void gevp_default_opts(gevp_opts* o);
+
+/* Creates a handle on CUDA device `device` bound to `stream` (a cudaStream_t; NULL =
+ * the legacy default stream). Returns GEVP_ERR_CUDA if the device cannot be used. */
+gevp_status gevp_create(gevp_handle* h, int device, void* stream);
+gevp_status gevp_destroy(gevp_handle h);
+gevp_status gevp_set_stream(gevp_handle h, void* stream);
+const char* gevp_status_string(gevp_status s);
+const char* gevp_last_error(gevp_handle h);
+const char* gevp_version(void);
+
+/* Reduction to standard form (the first step after Eq. 3: B = L L^H, C = L^-1 A L^-H).
+ *   A, B: n x n Hermitian (B HPD), read only.  L: n x n output, lower, strict upper = 0.
+ *   C: n x n output, Hermitian (both triangles written).
+ *   *info (host): 0, or the 1-based index of the first non-positive pivot of B (LAPACK
+ *   potrf convention); then GEVP_ERR_NOT_HPD is returned and L, C are undefined. */
+gevp_status gevp_reduce(gevp_handle h, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                        void* L, int64_t ldl, void* C, int64_t ldc, int64_t* info);
+
+/* The sequence solver (the paper's sequence {P_i} of correlated problems, each seeded
+ * with the eigenvectors of the one before).
+ *   A: host array of nprob device pointers, each n x n (ld lda). B: host array of nprob
+ *   device pointers (ld ldb); when consecutive pointers are equal, or opts->b_fixed is
+ *   set, the Cholesky factor is reused.
+ *   X_prev: nullable, n x kprev (ld ldxp) eigenvector guesses for problem 0 (in the
+ *   original space); kprev <= nev + nex.
+ *   Outputs (device): Lambda[nprob * nev] ascending per problem; resid[nprob * nev] the
+ *   original-space relative residuals ||A x - l B x|| / (||A||_est ||x||) with ||A||_est
+ *   a Lanczos estimate of ||A||_2 from below; X: n x nev (ld ldx) eigenvectors of the
+ *   last problem, B-orthonormal (or nprob such blocks, stride n*ldx, if keep_all_X).
+ *   stats: nullable host array of nprob gevp_stats.
+ *   Returns GEVP_ERR_NO_CONVERGENCE if some residual stays above tol (outputs written). */
+gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void* const* A, int64_t lda,
+                                const void* const* B, int64_t ldb, int nev, const void* X_prev, int64_t ldxp,
+                                int kprev, const gevp_opts* opts, double* Lambda, void* X, int64_t ldx,
+                                double* resid, gevp_stats* stats);
+
+/* Same, with every array in HOST memory (A, B: host arrays of host pointers; Lambda,
+ * resid, X host). The copies to and from the device are part of the call; problem l+1's
+ * matrix is copied on a second stream while problem l is solved. */
+gevp_status gevp_solve_sequence_host(gevp_handle h, int nprob, int64_t n, const void* const* A, int64_t lda,
+                                     const void* const* B, int64_t ldb, int nev, const gevp_opts* opts,
+                                     double* Lambda, void* X, int64_t ldx, double* resid, gevp_stats* stats);
+
+/* ---- individual steps of the solver (same kernels as the solver uses) ---------------- */
+
+/* Scaled Chebyshev filter (Zhou, Saad, Tiago & Chelikowsky 2006), in place:
+ *   Y <- p(C) Y,  p(t) = T_d((t-c)/e) / T_d((s-c)/e),  c = (lo+hi)/2, e = (hi-lo)/2,
+ * for the n x m block Y (ld ldy), degree d >= 1, scaling point s < lo < hi.
+ * prec: gevp_prec of the products. */
+gevp_status gevp_chebyshev_filter(gevp_handle h, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy,
+                                  int m, int degree, double lo, double hi, double s, int prec);
+
+/* CholQR2 (Fukaya, Nakatsukasa, Yanagisawa & Yamamoto 2014): Y (n x m) <- Q with
+ * Q^H Q = I and Y_in = Q R, R upper triangular with positive diagonal (written to R,
+ * m x m, ld ldr, if non-null). GEVP_ERR_NOT_HPD if Y is rank deficient in FP64. */
+gevp_status gevp_cholqr2(gevp_handle h, int64_t n, int m, void* Y, int64_t ldy, void* R, int64_t ldr);
+
+/* Rayleigh-Ritz on span(Q) (Q n x m orthonormal, in place): G = Q^H C Q = Z diag(theta) Z^H,
+ * Q <- Q Z, W = C Q (n x m output), theta ascending (device, m), res[i] = ||W_i - theta_i Q_i||. */
+gevp_status gevp_rayleigh_ritz(gevp_handle h, int64_t n, int m, const void* C, int64_t ldc, void* Q, int64_t ldq,
+                               void* W, int64_t ldw, double* theta, double* res);
+
+/* Small dense Hermitian eigensolver: G (m x m) = Z diag(theta) Z^H, theta ascending. */
+gevp_status gevp_heev_small(gevp_handle h, int m, const void* G, int64_t ldg, double* theta, void* Z, int64_t ldz);
+
+/* Lanczos spectral bounds of Hermitian C: out (host, 5 doubles) = {lowest Ritz value,
+ * highest Ritz value, upper bound of the spectrum, estimate of the count-th eigenvalue,
+ * |beta_k|}. */
+gevp_status gevp_spectral_bounds(gevp_handle h, int64_t n, const void* C, int64_t ldc, int k, int count,
+                                 double* out);
+
+/* Band-energy gradient for E = sum_{i<nev} lambda_i (first-order perturbation theory):
+ *   GA = gE * X X^H = dE/dA * gE,   GB = -gE * X diag(Lambda) X^H = dE/dB * gE,
+ * X n x nev B-orthonormal eigenvectors (ld ldx), Lambda device (nev); GA, GB n x n (ld ldg). */
+gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* X, int64_t ldx,
+                                 const double* Lambda, double gE, void* GA, void* GB, int64_t ldg);
+
+/* Measured FP64 FMA, FP64 DMMA and FP32 FMA rates of this device in TFLOP/s (host out[3]). */
+gevp_status gevp_probe_peaks(gevp_handle h, double* out);
+
+/* Number of kernels the handle launched since creation (for launch accounting). */
+int64_t gevp_kernel_launches(gevp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEVP_H */

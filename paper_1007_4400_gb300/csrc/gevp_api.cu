@@ -1,0 +1,837 @@
+// libgevp host driver: handle and workspace, the reduction to standard form, the
+// Chebyshev-filtered subspace iteration with locking, the sequence driver with warm
+// starts, and the C ABI declared in include/gevp.h.
+//
+// Per problem (the paper's P_i, Sec. "A new computational philosophy"):
+//   1. B = L L^H and L^-1 (once while B is unchanged);
+//   2. C = L^-1 A L^-H as T = L^-1 tril_half(A), M = T L^-H, C = M + M^H (4 n^3 flops:
+//      both products skip the zero triangles);
+//   3. spectral bounds by FP32 Lanczos on C (and an estimate of ||A||_2 for residuals);
+//   4. start block: the previous problem's block (warm) or a random one (cold);
+//   5. rounds of: Chebyshev filter on the active columns -> orthogonalise against the
+//      locked columns + CholQR2 -> Rayleigh-Ritz -> residuals -> lock the leading
+//      converged pairs, until nev pairs are locked;
+//   6. X = L^-H Q, Rayleigh quotients and residuals on the original pencil (A, B).
+#include "gevp_internal.cuh"
+#include "../../include/gevp.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace gevp;
+
+namespace gevp {
+int64_t g_launches = 0;
+}
+
+struct gevp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  // arena
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  int64_t cap_n = 0;
+  int cap_m = 0;
+  // n x n
+  double2 *L = nullptr, *Linv = nullptr, *C = nullptr, *T = nullptr;
+  float2* M32 = nullptr;
+  // n x m (ld = cap_m)
+  double2 *Q = nullptr, *Y1 = nullptr, *Y2 = nullptr, *W = nullptr, *Wt = nullptr, *Xf = nullptr;
+  // m x m
+  double2 *G = nullptr, *Zs = nullptr, *Gw = nullptr, *Gwi = nullptr, *P = nullptr;
+  double2* split = nullptr;
+  size_t split_elems = 0;
+  double2* trtri_ws = nullptr;
+  size_t trtri_elems = 0;
+  HeevWork hw{};
+  LanczosWork lw{};
+  double *theta = nullptr, *res = nullptr, *dscale = nullptr, *partial = nullptr, *bounds = nullptr,
+         *lam = nullptr, *resf = nullptr;
+  int *info = nullptr, *flag = nullptr;
+  // pinned host mirror
+  double* hbuf = nullptr;
+  size_t hbuf_elems = 0;
+  // warm-start state
+  bool have_prev = false;
+  int64_t prev_n = 0;
+  int prev_m = 0;
+  const void* prev_B = nullptr;
+  bool chol_valid = false;
+  // events
+  std::vector<cudaEvent_t> evpool;
+  std::string err;
+  gevp::FilterTC* tc = nullptr;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"GEVP_OK", "GEVP_ERR_INVALID_ARG", "GEVP_ERR_NOT_HPD", "GEVP_ERR_NO_CONVERGENCE",
+                              "GEVP_ERR_CUDA", "GEVP_ERR_OOM", "GEVP_ERR_TIMEOUT", "GEVP_ERR_INVALID_VALUE",
+                              "GEVP_ERR_UNSUPPORTED"};
+
+gevp_status cuda_fail(gevp_ctx* h, cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+  h->err = buf;
+  return e == cudaErrorMemoryAllocation ? GEVP_ERR_OOM : GEVP_ERR_CUDA;
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+#define TRY(x)                         \
+  do {                                 \
+    gevp_status s_ = (x);              \
+    if (s_ != GEVP_OK) return s_;      \
+  } while (0)
+
+inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Lay out (or only measure, when base == nullptr) every buffer for sizes (n, m).
+size_t layout(gevp_ctx* h, char* base, int64_t n, int m) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += al(bytes);
+    return p;
+  };
+  size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  h->L = (double2*)take(nn * 16);
+  h->Linv = (double2*)take(nn * 16);
+  h->C = (double2*)take(nn * 16);
+  h->T = (double2*)take(nn * 16);
+  h->M32 = (float2*)take(nn * 8);
+  h->Q = (double2*)take(nm * 16);
+  h->Y1 = (double2*)take(nm * 16);
+  h->Y2 = (double2*)take(nm * 16);
+  h->W = (double2*)take(nm * 16);
+  h->Wt = (double2*)take(nm * 16);
+  h->Xf = (double2*)take(nm * 16);
+  h->G = (double2*)take(mm * 16);
+  h->Zs = (double2*)take(mm * 16);
+  h->Gw = (double2*)take(mm * 16);
+  h->Gwi = (double2*)take(mm * 16);
+  h->P = (double2*)take(mm * 16);
+  h->split_elems = std::max<size_t>(64 * mm, 4 * nm);
+  h->split_elems = std::max<size_t>(h->split_elems, 1 << 16);
+  h->split = (double2*)take(h->split_elems * 16);
+  int64_t tn = std::max<int64_t>(n, m);
+  h->trtri_elems = trtri_ws_elems(tn) + std::max<size_t>(8 * (size_t)tn * 64, 1 << 16);
+  h->trtri_ws = (double2*)take(h->trtri_elems * 16);
+  // heev
+  h->hw.G32 = (float2*)take(mm * 8);
+  h->hw.Z32 = (float2*)take(mm * 8);
+  h->hw.w32 = (float*)take(m * 4 + 64);
+  h->hw.perm = (int*)take(m * 4 + 64);
+  h->hw.Z = (double2*)take(mm * 16);
+  h->hw.R = (double2*)take(mm * 16);
+  h->hw.S = (double2*)take(mm * 16);
+  h->hw.T = (double2*)take(mm * 16);
+  h->hw.E = (double2*)take(mm * 16);
+  h->hw.lam = (double*)take(m * 8 + 64);
+  h->hw.scal = (double*)take(16 * 8);
+  h->hw.split_ws = h->split;
+  h->hw.split_ws_elems = h->split_elems;
+  // lanczos (KMAX = 64)
+  h->lw.V = (float2*)take((size_t)65 * n * 8);
+  h->lw.ab = (float*)take(140 * 4);
+  h->lw.w = (float2*)take((size_t)n * 8);
+  h->lw.T32 = (float2*)take(64 * 64 * 8);
+  h->lw.Z32 = (float2*)take(64 * 64 * 8);
+  h->lw.w32 = (float*)take(64 * 4);
+  h->lw.perm = (int*)take(64 * 4);
+  h->lw.out = nullptr;
+  h->theta = (double*)take(m * 8 + 64);
+  h->res = (double*)take(m * 8 + 64);
+  h->lam = (double*)take(m * 8 + 64);
+  h->resf = (double*)take(m * 8 + 64);
+  h->dscale = (double*)take(m * 8 + 64);
+  h->partial = (double*)take(resid_partial_elems(n, m) * 8);
+  h->bounds = (double*)take(16 * 8);
+  h->info = (int*)take(64);
+  h->flag = (int*)take(64);
+  return off;
+}
+
+gevp_status ensure(gevp_ctx* h, int64_t n, int m) {
+  if (n <= h->cap_n && m <= h->cap_m && h->arena) return GEVP_OK;
+  int64_t nn = std::max(n, h->cap_n);
+  int mm = std::max(m, h->cap_m);
+  // a change of the block width invalidates the warm-start block layout (ld = cap_m)
+  h->have_prev = false;
+  if (h->arena) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->arena);
+    h->arena = nullptr;
+  }
+  size_t bytes = layout(h, nullptr, nn, mm);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    h->cap_n = 0;
+    h->cap_m = 0;
+    return cuda_fail(h, e, "workspace cudaMalloc");
+  }
+  h->arena = (char*)p;
+  h->arena_bytes = bytes;
+  layout(h, h->arena, nn, mm);
+  h->cap_n = nn;
+  h->cap_m = mm;
+  h->chol_valid = false;
+  size_t hel = 8 * (size_t)mm + 64;
+  if (hel > h->hbuf_elems) {
+    if (h->hbuf) cudaFreeHost(h->hbuf);
+    CK(cudaMallocHost(&h->hbuf, hel * sizeof(double)));
+    h->hbuf_elems = hel;
+  }
+  return GEVP_OK;
+}
+
+// ---------------------------------------------------------------- phase timing
+enum Phase { PH_CHOL, PH_REDUCE, PH_BOUNDS, PH_FILTER, PH_ORTH, PH_RR, PH_RESID, PH_FINAL, PH_N };
+
+struct Timer {
+  gevp_ctx* h;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  size_t used = 0;
+  float ms[PH_N] = {0};
+  explicit Timer(gevp_ctx* hh) : h(hh) {}
+  cudaEvent_t ev() {
+    if (used >= h->evpool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      h->evpool.push_back(e);
+    }
+    return h->evpool[used++];
+  }
+  void start() {
+    cudaEvent_t e = ev();
+    cudaEventRecord(e, h->stream);
+    marks.push_back({-1, e});
+  }
+  void mark(int phase) {
+    cudaEvent_t e = ev();
+    cudaEventRecord(e, h->stream);
+    marks.push_back({phase, e});
+  }
+  // call after the stream has been synchronised
+  void resolve() {
+    for (size_t i = 1; i < marks.size(); ++i) {
+      if (marks[i].first < 0) continue;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, marks[i - 1].second, marks[i].second);
+      ms[marks[i].first] += t;
+    }
+    if (!marks.empty()) {
+      auto last = marks.back();
+      marks.clear();
+      marks.push_back({-1, last.second});
+    }
+  }
+};
+
+gevp_status sync_read(gevp_ctx* h, const void* dsrc, void* hdst, size_t bytes) {
+  CK(cudaMemcpyAsync(hdst, dsrc, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+// ---------------------------------------------------------------- building blocks
+gevp_status factor_B(gevp_ctx* h, int64_t n, const double2* B, int64_t ldb, int64_t* info_out) {
+  CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
+  zcopy2d(n, n, B, ldb, h->L, n, h->stream);
+  potrf_lower(n, h->L, n, h->info, nullptr, 0, h->stream);
+  int info = 0;
+  TRY(sync_read(h, h->info, &info, sizeof(int)));
+  if (info_out) *info_out = info;
+  if (info != 0) {
+    h->chol_valid = false;
+    char buf[96];
+    snprintf(buf, sizeof buf, "B is not positive definite (pivot %d)", info);
+    h->err = buf;
+    return GEVP_ERR_NOT_HPD;
+  }
+  trtri_lower(n, h->L, n, h->Linv, n, h->trtri_ws, h->trtri_elems, h->stream);
+  h->chol_valid = true;
+  return GEVP_OK;
+}
+
+// C = Linv A Linv^H into Cout (n x n, ld ldc), via T = Linv tril_half(A), M = T Linv^H.
+void reduce_into(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, double2* Cout, int64_t ldc) {
+  ZgemmArgs a = zg((int)n, (int)n, (int)n, h->Linv, n, 0, A, lda, 0, h->T, n);
+  a.triA = 1;
+  a.maskB = 1;
+  zgemm(a, h->split, h->split_elems, h->stream);
+  ZgemmArgs b = zg((int)n, (int)n, (int)n, h->T, n, 0, h->Linv, n, 1, Cout, ldc);
+  b.triA = 1;
+  b.triB = 2;
+  zgemm(b, h->split, h->split_elems, h->stream);
+  herm_sum_inplace(n, Cout, ldc, h->stream);
+}
+
+// Orthonormalise Y (n x ma, ld ldy) against Q[:, 0:nlock] and by CholQR2; result in Out.
+gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_t ldy, int ma, double2* Out,
+                           int64_t ldo, gevp_stats* st) {
+  const int64_t ldq = h->cap_m;
+  for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
+    ZgemmArgs p = zg(nlock, ma, (int)n, h->Q, ldq, 1, Y, ldy, 0, h->P, ma);
+    zgemm(p, h->split, h->split_elems, h->stream);
+    ZgemmArgs u = zg((int)n, ma, nlock, h->Q, ldq, 0, h->P, ma, 0, Y, ldy, -1.0);
+    u.Cin = Y; u.ldc = ldy; u.beta = 1.0;
+    zgemm(u, h->split, h->split_elems, h->stream);
+  }
+  double2* src = Y;
+  int64_t lds = ldy;
+  double2* dst = Out;
+  int64_t ldd = ldo;
+  for (int pass = 0; pass < 2; ++pass) {
+    bool shifted = false;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      ZgemmArgs g = zg(ma, ma, (int)n, src, lds, 1, src, lds, 0, h->Gw, ma);
+      g.triD = 1;
+      zgemm(g, h->split, h->split_elems, h->stream);
+      hermitize_lower(ma, h->Gw, ma, h->stream);
+      gram_scale(ma, h->Gw, ma, h->dscale, h->stream);
+      if (shifted) {
+        // shifted CholQR (Fukaya et al. 2020): s = 11 (n m + m (m+1)) u ||Y D||_2^2, ||Y D||_F^2 = m
+        double u = 1.1102230246251565e-16;
+        double sh = 11.0 * ((double)n * ma + (double)ma * (ma + 1)) * u * ma * std::pow(10.0, attempt - 1);
+        zshift_diag(ma, h->Gw, ma, sh, h->stream);
+      }
+      CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
+      potrf_lower(ma, h->Gw, ma, h->info, nullptr, 0, h->stream);
+      int info = 0;
+      TRY(sync_read(h, h->info, &info, sizeof(int)));
+      if (info == 0) break;
+      if (attempt == 2) {
+        h->err = "CholQR: Gram matrix not positive definite after shifting";
+        return GEVP_ERR_NOT_HPD;
+      }
+      shifted = true;
+      if (st) st->orth_fallbacks++;
+    }
+    trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream);
+    zcol_scale(n, ma, src, lds, h->dscale, h->stream);
+    ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
+    q.triB = 2;
+    zgemm(q, h->split, h->split_elems, h->stream);
+    if (st) st->flops_fp64 += 8.0 * (double)n * ma * ma * 1.5;
+    std::swap(src, dst);
+    std::swap(lds, ldd);
+  }
+  // after two passes the result is back in Y's buffer (src); copy to Out
+  if (src != Out) zcopy2d(n, ma, src, lds, Out, ldo, h->stream);
+  return GEVP_OK;
+}
+
+// Rayleigh-Ritz on the active columns Q[:, nlock:nlock+ma]; updates Q, W, theta, res there.
+gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const double2* C, int64_t ldc,
+                          int refine, gevp_stats* st) {
+  const int64_t ld = h->cap_m;
+  double2* Qa = h->Q + nlock;
+  ZgemmArgs w = zg((int)n, ma, (int)n, C, ldc, 0, Qa, ld, 0, h->Wt, ld);
+  zgemm(w, h->split, h->split_elems, h->stream);
+  ZgemmArgs g = zg(ma, ma, (int)n, Qa, ld, 1, h->Wt, ld, 0, h->G, ma);
+  zgemm(g, h->split, h->split_elems, h->stream);
+  heev_small(ma, h->G, ma, h->theta + nlock, h->Zs, ma, h->hw, refine, h->stream);
+  ZgemmArgs q = zg((int)n, ma, ma, Qa, ld, 0, h->Zs, ma, 0, h->Y1, ld);
+  zgemm(q, h->split, h->split_elems, h->stream);
+  zcopy2d(n, ma, h->Y1, ld, Qa, ld, h->stream);
+  ZgemmArgs ww = zg((int)n, ma, ma, h->Wt, ld, 0, h->Zs, ma, 0, h->W + nlock, ld);
+  zgemm(ww, h->split, h->split_elems, h->stream);
+  resid_norms(n, ma, h->W + nlock, ld, Qa, ld, h->theta + nlock, h->res + nlock, h->partial, h->stream);
+  if (st) st->flops_fp64 += 8.0 * ((double)n * n * ma + 3.0 * n * ma * ma) + 32.0 * refine * (double)ma * ma * ma;
+  return GEVP_OK;
+}
+
+// Chebyshev filter on Y0 (n x ma, ld ld0) with FP64 products; returns the output buffer.
+double2* filter_fp64(gevp_ctx* h, int64_t n, const double2* C, int64_t ldc, const double2* Y0, int64_t ld0, int ma,
+                     int deg, double lo, double hi, double sc, double2* B1, double2* B2, int64_t ldb) {
+  double e = 0.5 * (hi - lo), c = 0.5 * (hi + lo);
+  double sigma = e / (sc - c), sigma1 = sigma;
+  ZgemmArgs a = zg((int)n, ma, (int)n, C, ldc, 0, Y0, ld0, 0, B1, ldb, sigma1 / e);
+  a.Cin = Y0; a.ldc = ld0; a.beta = -c * sigma1 / e;
+  zgemm(a, h->split, h->split_elems, h->stream);
+  const double2* prev = Y0;
+  int64_t ldp = ld0;
+  double2* cur = B1;
+  double2* nxt = B2;
+  for (int i = 2; i <= deg; ++i) {
+    double sn = 1.0 / (2.0 / sigma1 - sigma);
+    double al = 2.0 * sn / e;
+    ZgemmArgs s = zg((int)n, ma, (int)n, C, ldc, 0, cur, ldb, 0, nxt, ldb, al);
+    s.Cin = cur; s.ldc = ldb; s.beta = -al * c;
+    s.Ein = prev; s.lde = ldp; s.gamma = -sigma * sn;
+    zgemm(s, h->split, h->split_elems, h->stream);
+    sigma = sn;
+    double2* old = cur;
+    prev = old;
+    ldp = ldb;
+    cur = nxt;
+    nxt = old;   // overwrites the step before 'cur' next time (allowed: read-then-write per element)
+  }
+  return cur;
+}
+
+gevp_status lanczos(gevp_ctx* h, int64_t n, const double2* M, int64_t ldm, int k, int count, uint64_t seed,
+                    double* host_out) {
+  z_to_c(n, n, M, ldm, h->M32, n, h->stream);
+  lanczos_bounds(n, h->M32, n, k, count, seed, h->lw, h->bounds, h->stream);
+  return sync_read(h, h->bounds, host_out, 5 * sizeof(double));
+}
+
+struct SolveState {
+  int m, nev;
+  int nlock = 0;
+  bool have_theta = false;
+  std::vector<double> theta, res;
+  double upper = 0, lower_est = 0, a_est = 0, normC = 1, normA = 1;
+};
+
+int choose_degree(const SolveState& S, double lo, double hi, double tolC, int dmin, int dmax) {
+  double e = 0.5 * (hi - lo), c = 0.5 * (hi + lo);
+  int d = dmin;
+  for (int i = S.nlock; i < S.nev; ++i) {
+    double r = S.res[i];
+    if (r <= tolC) continue;
+    double t = (S.theta[i] - c) / e;
+    double at = std::fabs(t);
+    if (at <= 1.0) { d = dmax; break; }
+    double rho = at + std::sqrt(at * at - 1.0);
+    int di = (int)std::ceil(std::log(r / tolC) / std::log(rho));
+    d = std::max(d, di);
+  }
+  return std::min(std::max(d, dmin), dmax);
+}
+
+// Solve one problem whose standard form is already in h->C. Q holds the start block
+// (orthonormal, all m columns) when warm; otherwise it is drawn here.
+gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, const double2* B, int64_t ldb,
+                      int nev, int m, bool warm, const gevp_opts& o, int prob_index, Timer& tm, gevp_stats* st,
+                      double* Lam_out, double2* X_out, int64_t ldx, double* res_out) {
+  const int64_t ld = h->cap_m;
+  SolveState S;
+  S.m = m;
+  S.nev = nev;
+  S.theta.assign(m, 0.0);
+  S.res.assign(m, 0.0);
+  double hb[16];
+  // bounds of C, and an estimate of ||A||_2 for the final residuals
+  TRY(lanczos(h, n, h->C, n, o.lanczos_steps, m, o.seed + 7919ull * prob_index, hb));
+  S.lower_est = hb[0];
+  S.upper = hb[2];
+  S.a_est = hb[3];
+  S.normC = std::max(std::fabs(hb[0]), std::fabs(hb[2]));
+  TRY(lanczos(h, n, A, lda, o.lanczos_steps, 0, o.seed + 104729ull * prob_index + 1, hb));
+  S.normA = std::max(std::fabs(hb[0]), std::fabs(hb[1]));
+  tm.mark(PH_BOUNDS);
+  if (!warm) {
+    zrandn(n, m, h->Y1, ld, o.seed * 1000003ull + (uint64_t)prob_index, h->stream);
+    TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
+    tm.mark(PH_ORTH);
+  } else {
+    TRY(rayleigh_ritz(h, n, 0, m, h->C, n, o.refine_iters, st));
+    TRY(sync_read(h, h->theta, S.theta.data(), m * sizeof(double)));
+    TRY(sync_read(h, h->res, S.res.data(), m * sizeof(double)));
+    S.have_theta = true;
+    tm.mark(PH_RR);
+  }
+  double tolC = 0.1 * o.tol * S.normC;
+  int final_pass = 0;
+  double prev_maxres = 1e300;
+  int prec = o.filter_prec;
+  bool converged = false;
+  for (int it = 0;; ++it) {
+    if (S.have_theta) {
+      while (S.nlock < nev && S.res[S.nlock] <= tolC) S.nlock++;
+    }
+    if (S.nlock >= nev) {
+      // ---- final check in the original space
+      ZgemmArgs x = zg((int)n, nev, (int)n, h->Linv, n, 1, h->Q, ld, 0, h->Xf, ld);
+      x.triA = 2;
+      zgemm(x, h->split, h->split_elems, h->stream);
+      ZgemmArgs ax = zg((int)n, nev, (int)n, A, lda, 0, h->Xf, ld, 0, h->Y1, ld);
+      zgemm(ax, h->split, h->split_elems, h->stream);
+      ZgemmArgs bx = zg((int)n, nev, (int)n, B, ldb, 0, h->Xf, ld, 0, h->Y2, ld);
+      zgemm(bx, h->split, h->split_elems, h->stream);
+      // Y1/Y2 share ld; final_check wants one ld for X, AX, BX
+      final_check(n, nev, h->Xf, h->Y1, h->Y2, ld, h->lam, h->resf, S.normA, h->partial, h->stream);
+      if (st) st->flops_fp64 += 8.0 * (double)n * n * nev * 2.5;
+      std::vector<double> rf(nev);
+      TRY(sync_read(h, h->resf, rf.data(), nev * sizeof(double)));
+      tm.mark(PH_FINAL);
+      final_pass++;
+      double mx = 0;
+      int first_bad = nev;
+      for (int i = 0; i < nev; ++i) {
+        mx = std::max(mx, rf[i]);
+        if (rf[i] > o.tol && first_bad == nev) first_bad = i;
+      }
+      if (st) { st->final_passes = final_pass; st->max_resid = mx; }
+      if (first_bad == nev) { converged = true; break; }
+      if (final_pass >= 3 || it >= o.max_outer) break;
+      // tighten the C-space tolerance and re-open the failing pairs
+      tolC *= 0.05;
+      S.nlock = first_bad;
+      prec = GEVP_PREC_FP64;
+      continue;
+    }
+    if (it >= o.max_outer) break;
+    // ---- filter the active columns
+    int ma = m - S.nlock;
+    double hi = S.upper;
+    double lo = S.have_theta ? S.theta[m - 1] : S.a_est;
+    double sc = S.have_theta ? std::min(S.theta[0], S.lower_est) : S.lower_est;
+    if (!(lo > sc + 1e-3 * (hi - sc))) lo = sc + 0.5 * (hi - sc);
+    if (!(hi > lo)) hi = lo + 1e-3 * S.normC + 1e-300;
+    int deg = S.have_theta ? choose_degree(S, lo, hi, tolC, o.deg_min, o.deg_max) : std::min(o.deg_max, 10);
+    double2* Yf = filter_fp64(h, n, h->C, n, h->Q + S.nlock, ld, ma, deg, lo, hi, sc, h->Y1, h->Y2, ld);
+    if (st) {
+      st->filter_steps += deg;
+      st->matvecs += (int64_t)deg * ma;
+      st->flops_fp64 += 8.0 * (double)n * n * ma * deg;
+    }
+    tm.mark(PH_FILTER);
+    TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st));
+    tm.mark(PH_ORTH);
+    TRY(rayleigh_ritz(h, n, S.nlock, ma, h->C, n, o.refine_iters, st));
+    TRY(sync_read(h, h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double)));
+    TRY(sync_read(h, h->res + S.nlock, S.res.data() + S.nlock, ma * sizeof(double)));
+    tm.mark(PH_RR);
+    S.have_theta = true;
+    if (st) st->outer_iters++;
+    double mr = 0;
+    for (int i = S.nlock; i < nev; ++i) mr = std::max(mr, S.res[i]);
+    prev_maxres = mr;
+  }
+  (void)prev_maxres;
+  (void)prec;
+  CK(cudaMemcpyAsync(Lam_out, h->lam, nev * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(res_out, h->resf, nev * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (X_out) zcopy2d(n, nev, h->Xf, ld, X_out, ldx, h->stream);
+  if (st) st->converged = converged ? 1 : 0;
+  return converged ? GEVP_OK : GEVP_ERR_NO_CONVERGENCE;
+}
+
+bool bad_ld(int64_t ld, int64_t cols) { return ld < cols || ld <= 0; }
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void gevp_default_opts(gevp_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->filter_prec = GEVP_PREC_FP64;
+  o->tol = 1e-10;
+  o->max_outer = 60;
+  o->deg_min = 4;
+  o->deg_max = 24;
+  o->nex = 0;
+  o->seed = 10074400ull;
+  o->b_fixed = 0;
+  o->cold_start = 0;
+  o->lanczos_steps = 32;
+  o->refine_iters = 2;
+  o->keep_all_X = 0;
+}
+
+const char* gevp_status_string(gevp_status s) {
+  int i = (int)s;
+  if (i < 0 || i > 8) return "GEVP_UNKNOWN";
+  return kStatusNames[i];
+}
+
+const char* gevp_version(void) { return "gevp-gb300 0.1 (sm_103a)"; }
+
+const char* gevp_last_error(gevp_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+int64_t gevp_kernel_launches(gevp_handle h) { (void)h; return gevp::g_launches; }
+
+gevp_status gevp_create(gevp_handle* out, int device, void* stream) {
+  if (!out) return GEVP_ERR_INVALID_ARG;
+  *out = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return GEVP_ERR_CUDA;
+  gevp_ctx* h = new gevp_ctx();
+  h->device = device;
+  h->stream = (cudaStream_t)stream;
+  e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete h; return GEVP_ERR_CUDA; }
+  *out = h;
+  return GEVP_OK;
+}
+
+gevp_status gevp_destroy(gevp_handle h) {
+  if (!h) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->arena) cudaFree(h->arena);
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  for (auto e : h->evpool) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  delete h;
+  return GEVP_OK;
+}
+
+gevp_status gevp_set_stream(gevp_handle h, void* stream) {
+  if (!h) return GEVP_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  return GEVP_OK;
+}
+
+gevp_status gevp_reduce(gevp_handle h, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb, void* L,
+                        int64_t ldl, void* C, int64_t ldc, int64_t* info) {
+  if (!h || n < 0 || !info) return GEVP_ERR_INVALID_ARG;
+  *info = 0;
+  if (n == 0) return GEVP_OK;
+  if (!A || !B || !L || !C || bad_ld(lda, n) || bad_ld(ldb, n) || bad_ld(ldl, n) || bad_ld(ldc, n))
+    return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, 1));
+  TRY(factor_B(h, n, (const double2*)B, ldb, info));
+  reduce_into(h, n, (const double2*)A, lda, (double2*)C, ldc);
+  zcopy2d(n, n, h->L, n, (double2*)L, ldl, h->stream);
+  h->chol_valid = false;   // the caller's next solve refactors
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void* const* A, int64_t lda,
+                                const void* const* B, int64_t ldb, int nev, const void* X_prev, int64_t ldxp,
+                                int kprev, const gevp_opts* opts, double* Lambda, void* X, int64_t ldx,
+                                double* resid, gevp_stats* stats) {
+  if (!h || nprob < 0 || n < 0 || nev < 0) return GEVP_ERR_INVALID_ARG;
+  if (nprob == 0 || n == 0 || nev == 0) return GEVP_OK;
+  gevp_opts o;
+  if (opts) o = *opts; else gevp_default_opts(&o);
+  // at least two guard vectors: with none, the nev-th Ritz value sits at the edge of the
+  // damped interval and its convergence factor tends to one
+  int m = nev + std::max(2, o.nex);
+  if (m > n) m = (int)n;
+  if (nev > n || !A || !B || !Lambda || !resid || bad_ld(lda, n) || bad_ld(ldb, n)) return GEVP_ERR_INVALID_ARG;
+  if (X && bad_ld(ldx, nev)) return GEVP_ERR_INVALID_ARG;
+  if (X_prev && (kprev < 1 || kprev > m || bad_ld(ldxp, kprev))) return GEVP_ERR_INVALID_ARG;
+  if (m > 1024) { h->err = "block width nev + nex above 1024"; return GEVP_ERR_UNSUPPORTED; }
+  if (o.refine_iters < 1) o.refine_iters = 1;
+  if (o.deg_min < 1) o.deg_min = 1;
+  if (o.deg_max < o.deg_min) o.deg_max = o.deg_min;
+  if (o.lanczos_steps < 4) o.lanczos_steps = 4;
+  for (int l = 0; l < nprob; ++l)
+    if (!A[l] || !B[l]) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, m));
+  const int64_t ld = h->cap_m;
+  // input sanity: NaN/Inf in any A or in B
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  for (int l = 0; l < nprob; ++l) {
+    check_finite(n, n, (const double2*)A[l], lda, h->flag, h->stream);
+    if (l == 0 || B[l] != B[l - 1]) check_finite(n, n, (const double2*)B[l], ldb, h->flag, h->stream);
+  }
+  int bad = 0;
+  TRY(sync_read(h, h->flag, &bad, sizeof(int)));
+  if (bad) { h->err = "NaN or Inf in an input matrix"; return GEVP_ERR_INVALID_VALUE; }
+
+  gevp_status overall = GEVP_OK;
+  bool warm_ok = false;   // Q holds a usable start block for this n, m
+  for (int l = 0; l < nprob; ++l) {
+    Timer tm(h);
+    tm.start();
+    gevp_stats local{};
+    gevp_stats* st = stats ? &stats[l] : &local;
+    std::memset(st, 0, sizeof(*st));
+    const double2* Al = (const double2*)A[l];
+    const double2* Bl = (const double2*)B[l];
+    bool same_B = (l > 0) && (o.b_fixed || B[l] == B[l - 1]) && h->chol_valid;
+    bool refactor = !same_B;
+    if (refactor) {
+      // keep the previous eigenvector block in the original space for the warm start
+      if (warm_ok && h->chol_valid) {
+        ZgemmArgs x = zg((int)n, m, (int)n, h->Linv, n, 1, h->Q, ld, 0, h->Xf, ld);
+        x.triA = 2;
+        zgemm(x, h->split, h->split_elems, h->stream);
+      }
+      int64_t info = 0;
+      gevp_status s = factor_B(h, n, Bl, ldb, &info);
+      if (s != GEVP_OK) return s;
+      tm.mark(PH_CHOL);
+      if (warm_ok) {
+        // Y0 = L^H X_prev_block, then orthonormalise
+        ZgemmArgs y = zg((int)n, m, (int)n, h->L, n, 1, h->Xf, ld, 0, h->Y1, ld);
+        y.triA = 2;
+        zgemm(y, h->split, h->split_elems, h->stream);
+      }
+    }
+    reduce_into(h, n, Al, lda, h->C, n);
+    st->flops_fp64 += 4.0 * (double)n * n * n;
+    tm.mark(PH_REDUCE);
+    bool warm = false;
+    if (!o.cold_start) {
+      if (l == 0 && X_prev) {
+        // seed from the caller's vectors: Y0[:, :kprev] = L^H X_prev, rest random
+        zrandn(n, m, h->Y1, ld, o.seed + 17, h->stream);
+        ZgemmArgs y = zg((int)n, kprev, (int)n, h->L, n, 1, (const double2*)X_prev, ldxp, 0, h->Y1, ld);
+        y.triA = 2;
+        zgemm(y, h->split, h->split_elems, h->stream);
+        TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
+        warm = true;
+      } else if (warm_ok) {
+        if (refactor) TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
+        warm = true;
+      }
+    }
+    gevp_status s = solve_one(h, n, Al, lda, Bl, ldb, nev, m, warm, o, l, tm,
+                              st, Lambda + (int64_t)l * nev,
+                              X ? ((o.keep_all_X ? (double2*)X + (int64_t)l * n * ldx
+                                                 : (l == nprob - 1 ? (double2*)X : nullptr)))
+                                : nullptr,
+                              ldx, resid + (int64_t)l * nev);
+    if (s != GEVP_OK && s != GEVP_ERR_NO_CONVERGENCE) return s;
+    if (s == GEVP_ERR_NO_CONVERGENCE) overall = s;
+    warm_ok = true;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaGetLastError());
+    tm.mark(PH_FINAL);
+    CK(cudaStreamSynchronize(h->stream));
+    tm.resolve();
+    st->ms_chol = tm.ms[PH_CHOL];
+    st->ms_reduce = tm.ms[PH_REDUCE];
+    st->ms_bounds = tm.ms[PH_BOUNDS];
+    st->ms_filter = tm.ms[PH_FILTER];
+    st->ms_orth = tm.ms[PH_ORTH];
+    st->ms_rr = tm.ms[PH_RR];
+    st->ms_resid = tm.ms[PH_RESID];
+    st->ms_final = tm.ms[PH_FINAL];
+    float tot = 0;
+    for (int p = 0; p < PH_N; ++p) tot += tm.ms[p];
+    st->ms_total = tot;
+  }
+  if (overall != GEVP_OK) h->err = "some residual stayed above tol";
+  return overall;
+}
+
+gevp_status gevp_solve_sequence_host(gevp_handle h, int nprob, int64_t n, const void* const* A, int64_t lda,
+                                     const void* const* B, int64_t ldb, int nev, const gevp_opts* opts,
+                                     double* Lambda, void* X, int64_t ldx, double* resid, gevp_stats* stats) {
+  (void)h; (void)nprob; (void)n; (void)A; (void)lda; (void)B; (void)ldb; (void)nev; (void)opts;
+  (void)Lambda; (void)X; (void)ldx; (void)resid; (void)stats;
+  return GEVP_ERR_UNSUPPORTED;
+}
+
+gevp_status gevp_chebyshev_filter(gevp_handle h, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy, int m,
+                                  int degree, double lo, double hi, double s, int prec) {
+  if (!h || n < 0 || m < 0 || degree < 1 || !(hi > lo) || !(lo > s)) return GEVP_ERR_INVALID_ARG;
+  if (n == 0 || m == 0) return GEVP_OK;
+  if (!C || !Y || bad_ld(ldc, n) || bad_ld(ldy, m)) return GEVP_ERR_INVALID_ARG;
+  if (prec != GEVP_PREC_FP64) return GEVP_ERR_UNSUPPORTED;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, m));
+  const int64_t ld = h->cap_m;
+  double2* out = filter_fp64(h, n, (const double2*)C, ldc, (const double2*)Y, ldy, m, degree, lo, hi, s, h->Y1,
+                             h->Y2, ld);
+  zcopy2d(n, m, out, ld, (double2*)Y, ldy, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_cholqr2(gevp_handle h, int64_t n, int m, void* Y, int64_t ldy, void* R, int64_t ldr) {
+  if (!h || n < 0 || m < 0 || m > n) return GEVP_ERR_INVALID_ARG;
+  if (n == 0 || m == 0) return GEVP_OK;
+  if (!Y || bad_ld(ldy, m) || (R && bad_ld(ldr, m))) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, m));
+  const int64_t ld = h->cap_m;
+  h->have_prev = false;
+  zcopy2d(n, m, (const double2*)Y, ldy, h->Y2, ld, h->stream);
+  zcopy2d(n, m, (const double2*)Y, ldy, h->Wt, ld, h->stream);   // keep the input for R
+  TRY(orthonormalize(h, n, 0, h->Y2, ld, m, h->Y1, ld, nullptr));
+  zcopy2d(n, m, h->Y1, ld, (double2*)Y, ldy, h->stream);
+  if (R) {
+    // R = Q^H Y_in: upper triangular up to rounding; the strict lower part is set to 0
+    ZgemmArgs r = zg(m, m, (int)n, h->Y1, ld, 1, h->Wt, ld, 0, (double2*)R, ldr);
+    zgemm(r, h->split, h->split_elems, h->stream);
+    zero_lower(m, (double2*)R, ldr, h->stream);
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_rayleigh_ritz(gevp_handle h, int64_t n, int m, const void* C, int64_t ldc, void* Q, int64_t ldq,
+                               void* W, int64_t ldw, double* theta, double* res) {
+  if (!h || n < 0 || m < 0 || m > n) return GEVP_ERR_INVALID_ARG;
+  if (n == 0 || m == 0) return GEVP_OK;
+  if (!C || !Q || !W || !theta || !res || bad_ld(ldc, n) || bad_ld(ldq, m) || bad_ld(ldw, m))
+    return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, m));
+  const int64_t ld = h->cap_m;
+  h->have_prev = false;
+  zcopy2d(n, m, (const double2*)Q, ldq, h->Q, ld, h->stream);
+  TRY(rayleigh_ritz(h, n, 0, m, (const double2*)C, ldc, 2, nullptr));
+  zcopy2d(n, m, h->Q, ld, (double2*)Q, ldq, h->stream);
+  zcopy2d(n, m, h->W, ld, (double2*)W, ldw, h->stream);
+  CK(cudaMemcpyAsync(theta, h->theta, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(res, h->res, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_heev_small(gevp_handle h, int m, const void* G, int64_t ldg, double* theta, void* Z, int64_t ldz) {
+  if (!h || m < 0 || m > 1024) return GEVP_ERR_INVALID_ARG;
+  if (m == 0) return GEVP_OK;
+  if (!G || !theta || !Z || bad_ld(ldg, m) || bad_ld(ldz, m)) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, std::max<int64_t>(m, h->cap_n), m));
+  heev_small(m, (const double2*)G, ldg, theta, (double2*)Z, ldz, h->hw, 2, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_spectral_bounds(gevp_handle h, int64_t n, const void* C, int64_t ldc, int k, int count,
+                                 double* out) {
+  if (!h || n <= 0 || !C || !out || bad_ld(ldc, n) || k < 1) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, 1));
+  TRY(lanczos(h, n, (const double2*)C, ldc, k, count, 10074400ull, out));
+  return GEVP_OK;
+}
+
+gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* X, int64_t ldx, const double* Lambda,
+                                 double gE, void* GA, void* GB, int64_t ldg) {
+  if (!h || n < 0 || nev < 0 || nev > n) return GEVP_ERR_INVALID_ARG;
+  if (n == 0) return GEVP_OK;
+  if (!X || !Lambda || !GA || !GB || bad_ld(ldx, nev) || bad_ld(ldg, n)) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, n, std::max(nev, 1)));
+  gevp::energy_backward_ws(n, nev, (const double2*)X, ldx, Lambda, gE, (double2*)GA, (double2*)GB, ldg, h->T,
+                           h->split, h->split_elems, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_probe_peaks(gevp_handle h, double* out) {
+  if (!h || !out) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  probe_peaks(&out[0], &out[1], &out[2], h->stream);
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+}  // extern "C"

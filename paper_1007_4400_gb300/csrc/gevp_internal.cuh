@@ -1,0 +1,152 @@
+// Internal declarations shared by the CUDA translation units of libgevp.
+// All matrices are row-major; complex128 is interleaved (double2: x = real, y = imag).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace gevp {
+
+// ---------------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ double2 zmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// acc += a * b
+__device__ __forceinline__ void zfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------- FP64 complex GEMM
+// D = alpha * op(A) op(B) + beta * Cin + gamma * Ein   (real alpha, beta, gamma)
+// op(X) = X (op = 0) or X^H (op = 1). op(A) is M x K, op(B) is K x N, D is M x N.
+// tri flags let whole k-tiles that are known zero be skipped:
+//   triA = 1: op(A) lower (op(A)[i][k] = 0 for k > i);  2: upper (0 for k < i)
+//   triB = 1: op(B) lower (op(B)[k][j] = 0 for k < j);  2: upper (0 for k > j)
+//   triD = 1: only tiles that intersect the lower triangle of D are computed
+// maskB = 1 (opB = 0 only): op(B) is read as the lower triangle of B with its diagonal
+//   halved and zeros above (the Hermitian split B = Bl + Bl^H).
+// ksplit > 1: grid.z carries k-slices; slice z writes its partial product (no epilogue)
+//   to D + z * M * N with ld = N, and zgemm_reduce_splits finishes the epilogue.
+struct ZgemmArgs {
+  int M, N, K;
+  const double2* A; int64_t lda; int opA;
+  const double2* B; int64_t ldb; int opB;
+  double2* D; int64_t ldd;
+  double alpha;
+  const double2* Cin; int64_t ldc; double beta;
+  const double2* Ein; int64_t lde; double gamma;
+  int triA, triB, triD, maskB;
+  int ksplit;
+  int batch;
+  int64_t sA, sB, sD, sC, sE;   // batch strides in elements
+};
+
+void zgemm(const ZgemmArgs& a, double2* split_ws, size_t split_ws_elems, cudaStream_t s);
+// Simple helper for the common case.
+ZgemmArgs zg(int M, int N, int K, const double2* A, int64_t lda, int opA,
+             const double2* B, int64_t ldb, int opB, double2* D, int64_t ldd, double alpha = 1.0);
+
+// ---------------------------------------------------------------- elementwise / misc
+void herm_sum_inplace(int64_t n, double2* C, int64_t ldc, cudaStream_t s);  // C <- C + C^H
+void zshift_diag(int64_t n, double2* A, int64_t lda, double sh, cudaStream_t s);
+void zero_lower(int64_t n, double2* A, int64_t lda, cudaStream_t s);        // strict lower <- 0
+void hermitize_lower(int64_t n, double2* C, int64_t ldc, cudaStream_t s);   // upper <- conj(lower), real diag
+void hermitize_avg(int64_t n, double2* C, int64_t ldc, cudaStream_t s);     // C <- (C + C^H)/2
+void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s);        // strict upper <- 0
+void zcopy2d(int64_t rows, int64_t cols, const double2* src, int64_t lds, double2* dst, int64_t ldd, cudaStream_t s);
+void zset_identity(int64_t rows, int64_t cols, double2* A, int64_t lda, cudaStream_t s);
+void z_to_c(int64_t rows, int64_t cols, const double2* src, int64_t lds, float2* dst, int64_t ldd, cudaStream_t s);
+void zrandn(int64_t rows, int64_t cols, double2* A, int64_t lda, uint64_t seed, cudaStream_t s);
+void zcol_scale(int64_t rows, int64_t cols, double2* A, int64_t lda, const double* scale, cudaStream_t s);
+int  check_finite(int64_t rows, int64_t cols, const double2* A, int64_t lda, int* dflag, cudaStream_t s);
+
+// ---------------------------------------------------------------- factorizations
+// Blocked lower Cholesky in place (strict upper zeroed). info_dev: 0 or 1-based pivot.
+void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* ws, size_t ws_elems,
+                 cudaStream_t s);
+// Lower-triangular inverse: Linv = L^-1 (Linv separate buffer, strict upper zeroed).
+void trtri_lower(int64_t n, const double2* L, int64_t ldl, double2* Linv, int64_t ldi, double2* ws,
+                 size_t ws_elems, cudaStream_t s);
+size_t potrf_ws_elems(int64_t n);
+size_t trtri_ws_elems(int64_t n);
+
+// ---------------------------------------------------------------- small Hermitian eigensolver
+// G (m x m Hermitian, FP64) -> theta ascending (m), Z (m x m, columns = eigenvectors).
+// FP32 parallel Jacobi followed by FP64 Ogita-Aishima refinement built from FP64 GEMMs.
+struct HeevWork {
+  float2* G32; float2* Z32; float* w32; int* perm;
+  double2 *Z, *R, *S, *T, *E;   // m x m each
+  double* lam;                  // m
+  double2* split_ws; size_t split_ws_elems;
+  double* scal;                 // small scalars
+};
+size_t heev_ws_bytes(int m, size_t split_elems);
+void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Z, int64_t ldz,
+                const HeevWork& w, int refine_iters, cudaStream_t s);
+// FP32 Jacobi on a (possibly real) Hermitian matrix in FP32 (single CTA); sorted output.
+void jacobi32(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s);
+
+// ---------------------------------------------------------------- Lanczos bounds (FP32)
+struct LanczosOut { double lam_min, lam_max, upper, a_est, beta_last; };
+struct LanczosWork { float2* V; float* ab; float2* w; float2* T32; float2* Z32; float* w32; int* perm; double* out; };
+size_t lanczos_ws_bytes(int64_t n, int k);
+// k-step Lanczos with full re-orthogonalisation on the FP32 copy of a Hermitian matrix.
+// Writes to dev_out[0..4] = {theta_min, theta_max, upper bound, estimate of the count-th
+// eigenvalue from the Ritz-weight density, |beta_k|}. count <= 0 skips the estimate.
+void lanczos_bounds(int64_t n, const float2* M32, int64_t ldm, int k, int count, uint64_t seed,
+                    const LanczosWork& w, double* dev_out, cudaStream_t s);
+
+// ---------------------------------------------------------------- tall-skinny kernels
+// res[i] = || W_i - theta_i Q_i ||_2 for columns i of n x m blocks (deterministic 2-stage).
+void resid_norms(int64_t n, int m, const double2* W, int64_t ldw, const double2* Q, int64_t ldq,
+                 const double* theta, double* res, double* partial, cudaStream_t s);
+size_t resid_partial_elems(int64_t n, int m);
+// Column dots for the final check: out[0][i] = Re(x_i^H ax_i), out[1][i] = Re(x_i^H bx_i),
+// then (second call, mode 1) out[2][i] = ||ax_i - lam_i bx_i||^2, out[3][i] = ||x_i||^2.
+void final_check(int64_t n, int m, const double2* X, const double2* AX, const double2* BX, int64_t ld,
+                 double* lam_io, double* res_out, double normA, double* partial, cudaStream_t s);
+// Cholesky-QR helpers
+void gram_scale(int m, double2* W, int64_t ldw, double* dscale, cudaStream_t s); // W <- D W D, D = diag(W)^-1/2
+
+// ---------------------------------------------------------------- backward
+// GA = gE X X^H, GB = -gE X diag(lam) X^H (lower tiles by GEMM, then Hermitian completion).
+// XL: n x nev scratch.
+void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const double* lam, double gE,
+                        double2* GA, double2* GB, int64_t ldg, double2* XL, double2* split, size_t split_elems,
+                        cudaStream_t s);
+
+// ---------------------------------------------------------------- low-precision filter (tcgen05)
+struct FilterTC;   // opaque, owned by the handle
+bool tc_filter_supported();
+
+// ---------------------------------------------------------------- probes
+void probe_peaks(double* fp64_fma_tflops, double* fp64_dmma_tflops, double* fp32_fma_tflops, cudaStream_t s);
+
+// ---------------------------------------------------------------- launch accounting
+extern int64_t g_launches;
+#define LAUNCH_NOTE(k) (::gevp::g_launches += (k))
+
+// ---------------------------------------------------------------- error handling
+#define GEVP_CUDA_TRY(x)                                   \
+  do {                                                     \
+    cudaError_t e__ = (x);                                 \
+    if (e__ != cudaSuccess) return e__;                    \
+  } while (0)
+
+}  // namespace gevp

@@ -1,0 +1,309 @@
+// Small dense Hermitian eigensolver for the Rayleigh-Ritz projection (m <= a few hundred).
+//
+// One SM executes FP64 at about 1.7 FMA per clock on this part, so an FP64 Jacobi in one
+// CTA would take milliseconds. Instead:
+//   1. parallel-ordered two-sided Jacobi in FP32 in one CTA (FP32 runs at 128 FMA per
+//      clock per SM), giving eigenvectors accurate to about 1e-6;
+//   2. Ogita & Aishima's iterative refinement for symmetric/Hermitian eigenvector
+//      matrices (Japan J. Ind. Appl. Math. 35, 2018), which converges quadratically and
+//      consists of four FP64 GEMMs per step spread over all SMs; two steps reach FP64
+//      accuracy. Nearly coincident eigenvalues (closer than the refinement's delta) are
+//      treated as a cluster: their vectors stay an orthonormal basis of the cluster's
+//      invariant subspace, which is all the Rayleigh-Ritz step needs.
+#include "gevp_internal.cuh"
+#include <algorithm>
+
+namespace gevp {
+
+namespace {
+
+constexpr int JT = 1024;   // threads of the Jacobi CTA
+
+__device__ __forceinline__ void block_pair(int step, int k, int np, int* p, int* q) {
+  // circle method: position 0 fixed, the other np-1 players rotate by one per round
+  auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + step) % (np - 1)); };
+  int a = player(k), b = player(np - 1 - k);
+  *p = a < b ? a : b;
+  *q = a < b ? b : a;
+}
+
+__device__ float block_sum(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// G (m x m, FP32 complex, Hermitian) is destroyed; Z receives eigenvectors (columns);
+// w receives eigenvalues sorted ascending and perm the column order (w[k] = G[perm[k]]).
+__global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* Z, float* w, int* perm,
+                                                      int max_sweeps) {
+  __shared__ float4 U[512];       // per pair: (c, s, Re ph, Im ph)
+  __shared__ int PQ[512][2];
+  __shared__ float red[32];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += JT) Z[e] = make_float2((e / m) == (e % m) ? 1.f : 0.f, 0.f);
+  int np = (m % 2) ? m + 1 : m;
+  int npairs = np / 2;
+  float fro2 = 0.f;
+  for (int e = tid; e < m * m; e += JT) { float2 g = G[e]; fro2 += g.x * g.x + g.y * g.y; }
+  fro2 = block_sum(fro2, red);
+  const float tol2 = 1e-13f * fro2;   // (3.2e-7 * ||G||_F)^2
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
+    float off = 0.f;
+    for (int e = tid; e < m * m; e += JT) {
+      int i = e / m, j = e % m;
+      if (i != j) { float2 g = G[e]; off += g.x * g.x + g.y * g.y; }
+    }
+    off = block_sum(off, red);
+    if (off <= tol2) break;
+    for (int step = 0; step < np - 1; ++step) {
+      for (int k = tid; k < npairs; k += JT) {
+        int p, q;
+        block_pair(step, k, np, &p, &q);
+        PQ[k][0] = p;
+        PQ[k][1] = q;
+        float4 u = make_float4(1.f, 0.f, 1.f, 0.f);
+        if (q < m) {
+          float2 apq = G[p * m + q];
+          float r = sqrtf(apq.x * apq.x + apq.y * apq.y);
+          if (r > 1e-30f) {
+            float app = G[p * m + p].x, aqq = G[q * m + q].x;
+            float tau = (aqq - app) / (2.f * r);
+            float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            float c = rsqrtf(1.f + t * t);
+            u = make_float4(c, t * c, apq.x / r, apq.y / r);
+          }
+        }
+        U[k] = u;
+      }
+      __syncthreads();
+      // columns: G <- G U, Z <- Z U, with U = [[c, s], [-s conj(ph), c conj(ph)]]
+      for (int e = tid; e < m * npairs; e += JT) {
+        int i = e / npairs, k = e % npairs;
+        int p = PQ[k][0], q = PQ[k][1];
+        if (q >= m) continue;
+        float4 u = U[k];
+        float c = u.x, s = u.y;
+        float2 phc = make_float2(u.z, -u.w);
+        float2 gp = G[i * m + p], gq = G[i * m + q];
+        float2 gqph = make_float2(gq.x * phc.x - gq.y * phc.y, gq.x * phc.y + gq.y * phc.x);
+        G[i * m + p] = make_float2(c * gp.x - s * gqph.x, c * gp.y - s * gqph.y);
+        G[i * m + q] = make_float2(s * gp.x + c * gqph.x, s * gp.y + c * gqph.y);
+        float2 zp = Z[i * m + p], zq = Z[i * m + q];
+        float2 zqph = make_float2(zq.x * phc.x - zq.y * phc.y, zq.x * phc.y + zq.y * phc.x);
+        Z[i * m + p] = make_float2(c * zp.x - s * zqph.x, c * zp.y - s * zqph.y);
+        Z[i * m + q] = make_float2(s * zp.x + c * zqph.x, s * zp.y + c * zqph.y);
+      }
+      __syncthreads();
+      // rows: G <- U^H G ; U^H = [[c, -s ph], [s, c ph]]
+      for (int e = tid; e < m * npairs; e += JT) {
+        int k = e / m, j = e % m;
+        int p = PQ[k][0], q = PQ[k][1];
+        if (q >= m) continue;
+        float4 u = U[k];
+        float c = u.x, s = u.y;
+        float2 ph = make_float2(u.z, u.w);
+        float2 gp = G[p * m + j], gq = G[q * m + j];
+        float2 phgq = make_float2(ph.x * gq.x - ph.y * gq.y, ph.x * gq.y + ph.y * gq.x);
+        float2 np_ = make_float2(c * gp.x - s * phgq.x, c * gp.y - s * phgq.y);
+        float2 nq_ = make_float2(s * gp.x + c * phgq.x, s * gp.y + c * phgq.y);
+        if (j == q) np_ = make_float2(0.f, 0.f);
+        if (j == p) nq_ = make_float2(0.f, 0.f);
+        if (j == p) np_.y = 0.f;
+        if (j == q) nq_.y = 0.f;
+        G[p * m + j] = np_;
+        G[q * m + j] = nq_;
+      }
+      __syncthreads();
+    }
+  }
+  // sort ascending by rank (ties by index)
+  for (int i = tid; i < m; i += JT) {
+    float wi = G[i * m + i].x;
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      float wj = G[j * m + j].x;
+      r += (wj < wi) || (wj == wi && j < i);
+    }
+    perm[r] = i;
+    w[r] = wi;
+  }
+}
+
+// Z64[:, k] = Z32[:, perm[k]]
+__global__ void gather_z_kernel(int m, const float2* Z32, const int* perm, double2* Z, int64_t ldz) {
+  int64_t total = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), k = (int)(e % m);
+    float2 v = Z32[i * m + perm[k]];
+    Z[i * ldz + k] = make_double2(v.x, v.y);
+  }
+}
+
+__global__ void g_to_c_kernel(int m, const double2* G, int64_t ldg, float2* G32) {
+  int64_t total = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), j = (int)(e % m);
+    double2 a = G[i * ldg + j], b = G[j * ldg + i];   // Hermitian part
+    G32[e] = make_float2((float)(0.5 * (a.x + b.x)), (float)(0.5 * (a.y - b.y)));
+  }
+}
+
+__device__ double block_sum_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Ogita-Aishima: lam_i = Re S_ii / (1 - Re R_ii); delta = 2 (||S - diag(lam)||_F + ||G||_F ||R||_F).
+// scal[0] = delta, scal[1] = ||G||_F (input, computed once).
+__global__ void oa_scalars_kernel(int m, const double2* R, const double2* S, double* lam, double* scal) {
+  __shared__ double red[32];
+  double soff = 0.0, r2 = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    lam[i] = S[i * m + i].x / (1.0 - R[i * m + i].x);
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e / m, j = e % m;
+    double2 sv = S[e];
+    if (i == j) sv.x -= lam[i];
+    soff += zabs2(sv);
+    r2 += zabs2(R[e]);
+  }
+  soff = block_sum_d(soff, red);
+  r2 = block_sum_d(r2, red);
+  if (threadIdx.x == 0) scal[0] = 2.0 * (sqrt(soff) + scal[1] * sqrt(r2));
+}
+
+__global__ void oa_update_kernel(int m, const double2* R, const double2* S, const double* lam, const double* scal,
+                                 double2* E) {
+  int64_t total = (int64_t)m * m;
+  double delta = scal[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), j = (int)(e % m);
+    double2 r = R[e];
+    double2 v;
+    double d = lam[j] - lam[i];
+    if (i != j && fabs(d) > delta) {
+      double2 sv = S[e];
+      v = make_double2((sv.x + lam[j] * r.x) / d, (sv.y + lam[j] * r.y) / d);
+    } else {
+      v = zscale(r, 0.5);
+    }
+    E[e] = v;
+  }
+}
+
+__global__ void frob_kernel(int m, const double2* G, int64_t ldg, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) s += zabs2(G[(e / m) * ldg + (e % m)]);
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+
+// final ordering: theta ascending, Z columns permuted accordingly
+__global__ void sort_pairs_kernel(int m, const double* lam, const double2* Zin, double* theta, double2* Z,
+                                  int64_t ldz) {
+  __shared__ int rk[1024];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double li = lam[i];
+    int r = 0;
+    for (int j = 0; j < m; ++j) r += (lam[j] < li) || (lam[j] == li && j < i);
+    rk[i] = r;
+    theta[r] = li;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e / m, k = e % m;
+    Z[i * ldz + rk[k]] = Zin[i * m + k];
+  }
+}
+
+}  // namespace
+
+size_t heev_ws_bytes(int m, size_t split_elems) {
+  size_t mm = (size_t)m * m;
+  size_t b = 0;
+  b += 2 * mm * sizeof(float2) + m * sizeof(float) + m * sizeof(int);
+  b += 5 * mm * sizeof(double2) + m * sizeof(double) + 8 * sizeof(double);
+  b += split_elems * sizeof(double2);
+  return b + 16 * 256;
+}
+
+void jacobi32(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
+  jacobi32_kernel<<<1, JT, 0, s>>>(m, G, Z, w, perm, max_sweeps);
+  LAUNCH_NOTE(1);
+}
+
+void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zout, int64_t ldz,
+                const HeevWork& w, int refine_iters, cudaStream_t s) {
+  if (m <= 0) return;
+  int64_t mm = (int64_t)m * m;
+  int blocks = (int)std::min<int64_t>((mm + 255) / 256, 152 * 4);
+  g_to_c_kernel<<<blocks, 256, 0, s>>>(m, G, ldg, w.G32);
+  LAUNCH_NOTE(1);
+  jacobi32_kernel<<<1, JT, 0, s>>>(m, w.G32, w.Z32, w.w32, w.perm, 30);
+  LAUNCH_NOTE(1);
+  gather_z_kernel<<<blocks, 256, 0, s>>>(m, w.Z32, w.perm, w.Z, m);
+  LAUNCH_NOTE(1);
+  frob_kernel<<<1, 1024, 0, s>>>(m, G, ldg, w.scal + 1);
+  LAUNCH_NOTE(1);
+  double2* Z = w.Z;
+  double2* Zn = w.T;   // ping-pong partner
+  for (int it = 0; it < refine_iters; ++it) {
+    // R = I - Z^H Z
+    zset_identity(m, m, w.R, m, s);
+    ZgemmArgs a = zg(m, m, m, Z, m, 1, Z, m, 0, w.R, m, -1.0);
+    a.Cin = w.R; a.ldc = m; a.beta = 1.0;
+    zgemm(a, w.split_ws, w.split_ws_elems, s);
+    // E <- G Z (E used as scratch), S = Z^H (G Z)
+    ZgemmArgs b = zg(m, m, m, G, ldg, 0, Z, m, 0, w.E, m);
+    zgemm(b, w.split_ws, w.split_ws_elems, s);
+    ZgemmArgs c = zg(m, m, m, Z, m, 1, w.E, m, 0, w.S, m);
+    zgemm(c, w.split_ws, w.split_ws_elems, s);
+    oa_scalars_kernel<<<1, 1024, 0, s>>>(m, w.R, w.S, w.lam, w.scal);
+    LAUNCH_NOTE(1);
+    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E);
+    LAUNCH_NOTE(1);
+    // Zn = Z + Z E
+    ZgemmArgs d = zg(m, m, m, Z, m, 0, w.E, m, 0, Zn, m);
+    d.Cin = Z; d.ldc = m; d.beta = 1.0;
+    zgemm(d, w.split_ws, w.split_ws_elems, s);
+    std::swap(Z, Zn);
+  }
+  if (refine_iters == 0) {
+    // eigenvalues straight from the FP32 solve
+    // (theta written by the sort kernel from lam; fill lam from w32)
+    // convert on device via a tiny kernel: reuse sort on w32 cast
+  }
+  sort_pairs_kernel<<<1, 1024, 0, s>>>(m, w.lam, Z, theta, Zout, ldz);
+  LAUNCH_NOTE(1);
+}
+
+}  // namespace gevp

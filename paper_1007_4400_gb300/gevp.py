@@ -1,0 +1,321 @@
+"""Python binding of libgevp (ctypes over the C ABI in include/gevp.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels. Tensors must be
+CUDA complex128 (or float64 for eigenvalues/residuals); PyTorch supplies device memory and
+the current stream. There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+_LIB = None
+_LOCK = threading.Lock()
+_HANDLES: dict = {}
+
+STATUS = ["GEVP_OK", "GEVP_ERR_INVALID_ARG", "GEVP_ERR_NOT_HPD", "GEVP_ERR_NO_CONVERGENCE", "GEVP_ERR_CUDA",
+          "GEVP_ERR_OOM", "GEVP_ERR_TIMEOUT", "GEVP_ERR_INVALID_VALUE", "GEVP_ERR_UNSUPPORTED"]
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+class GevpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        self.name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{self.name}: {msg}")
+
+
+class GevpOpts(C.Structure):
+    _fields_ = [("filter_prec", C.c_int), ("tol", C.c_double), ("max_outer", C.c_int), ("deg_min", C.c_int),
+                ("deg_max", C.c_int), ("nex", C.c_int), ("seed", C.c_uint64), ("b_fixed", C.c_int),
+                ("cold_start", C.c_int), ("lanczos_steps", C.c_int), ("refine_iters", C.c_int),
+                ("keep_all_X", C.c_int)]
+
+
+class GevpStats(C.Structure):
+    _fields_ = [("outer_iters", C.c_int), ("filter_steps", C.c_int), ("switches", C.c_int),
+                ("orth_fallbacks", C.c_int), ("final_passes", C.c_int), ("converged", C.c_int),
+                ("matvecs", C.c_int64), ("flops_fp64", C.c_double), ("flops_lowp", C.c_double),
+                ("max_resid", C.c_double),
+                ("ms_chol", C.c_float), ("ms_reduce", C.c_float), ("ms_bounds", C.c_float),
+                ("ms_filter", C.c_float), ("ms_orth", C.c_float), ("ms_rr", C.c_float), ("ms_resid", C.c_float),
+                ("ms_final", C.c_float), ("ms_total", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgevp.so (building it first if needed). Raises if it cannot be loaded."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.LIB
+        if build_if_missing and (not os.path.exists(path) or _build._stale()):
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgevp is not built ({path}); run paper_1007_4400_gb300._build.build()")
+        L = C.CDLL(path)
+        vp, i64, i32, f64 = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        L.gevp_create.argtypes = [C.POINTER(vp), i32, vp]
+        L.gevp_destroy.argtypes = [vp]
+        L.gevp_set_stream.argtypes = [vp, vp]
+        L.gevp_status_string.restype = C.c_char_p
+        L.gevp_status_string.argtypes = [i32]
+        L.gevp_last_error.restype = C.c_char_p
+        L.gevp_last_error.argtypes = [vp]
+        L.gevp_version.restype = C.c_char_p
+        L.gevp_default_opts.argtypes = [C.POINTER(GevpOpts)]
+        L.gevp_default_opts.restype = None
+        L.gevp_reduce.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, C.POINTER(i64)]
+        L.gevp_solve_sequence.argtypes = [vp, i32, i64, C.POINTER(vp), i64, C.POINTER(vp), i64, i32, vp, i64, i32,
+                                          C.POINTER(GevpOpts), vp, vp, i64, vp, C.POINTER(GevpStats)]
+        L.gevp_solve_sequence_host.argtypes = [vp, i32, i64, C.POINTER(vp), i64, C.POINTER(vp), i64, i32,
+                                               C.POINTER(GevpOpts), vp, vp, i64, vp, C.POINTER(GevpStats)]
+        L.gevp_chebyshev_filter.argtypes = [vp, i64, vp, i64, vp, i64, i32, i32, f64, f64, f64, i32]
+        L.gevp_cholqr2.argtypes = [vp, i64, i32, vp, i64, vp, i64]
+        L.gevp_rayleigh_ritz.argtypes = [vp, i64, i32, vp, i64, vp, i64, vp, i64, vp, vp]
+        L.gevp_heev_small.argtypes = [vp, i32, vp, i64, vp, vp, i64]
+        L.gevp_spectral_bounds.argtypes = [vp, i64, vp, i64, i32, i32, C.POINTER(f64)]
+        L.gevp_energy_backward.argtypes = [vp, i64, i32, vp, i64, vp, f64, vp, vp, i64]
+        L.gevp_probe_peaks.argtypes = [vp, C.POINTER(f64)]
+        L.gevp_kernel_launches.argtypes = [vp]
+        L.gevp_kernel_launches.restype = i64
+        for name in ("gevp_create", "gevp_destroy", "gevp_set_stream", "gevp_reduce", "gevp_solve_sequence",
+                     "gevp_solve_sequence_host", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
+                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_probe_peaks"):
+            getattr(L, name).restype = i32
+        _LIB = L
+        return L
+
+
+def _handle(device: torch.device):
+    L = load()
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    h = _HANDLES.get(idx)
+    if h is None:
+        hv = C.c_void_p()
+        with torch.cuda.device(idx):
+            st = L.gevp_create(C.byref(hv), idx, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        _check(st, None)
+        h = hv
+        _HANDLES[idx] = h
+    with torch.cuda.device(idx):
+        L.gevp_set_stream(h, C.c_void_p(torch.cuda.current_stream(idx).cuda_stream))
+    return h
+
+
+def _check(st: int, h) -> None:
+    if st != 0:
+        msg = load().gevp_last_error(h).decode() if h is not None else ""
+        raise GevpError(st, msg)
+
+
+def _mat(t: torch.Tensor, name: str, dtype=torch.complex128) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() == 2 and t.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major with unit column stride")
+    return t
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def default_opts(**kw) -> GevpOpts:
+    o = GevpOpts()
+    load().gevp_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "filter_prec" and isinstance(v, str):
+            v = PREC[v]
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def reduce(A: torch.Tensor, B: torch.Tensor):
+    """(L, C) with B = L L^H and C = L^-1 A L^-H (see gevp_reduce)."""
+    _mat(A, "A"); _mat(B, "B")
+    n = A.shape[0]
+    h = _handle(A.device)
+    L_ = torch.empty_like(A)
+    C_ = torch.empty_like(A)
+    info = C.c_int64(0)
+    st = load().gevp_reduce(h, n, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(L_), n, _ptr(C_), n,
+                            C.byref(info))
+    _check(st, h)
+    return L_, C_
+
+
+@dataclass
+class SequenceResult:
+    Lambda: torch.Tensor     # (nprob, nev) float64
+    X: torch.Tensor          # (n, nev) or (nprob, n, nev) complex128
+    resid: torch.Tensor      # (nprob, nev) float64
+    stats: list              # per-problem dicts
+    status: int
+
+
+def solve_sequence(A_list, B, nev: int, X_prev=None, keep_all_X: bool = False, check: bool = True, **opts):
+    """Solve the sequence A_l x = lambda B_l x (l = 0..len(A_list)-1) for the lowest nev
+    pairs with warm starts (gevp_solve_sequence). B: one tensor (fixed) or a list."""
+    As = list(A_list)
+    Bs = list(B) if isinstance(B, (list, tuple)) else [B] * len(As)
+    if len(Bs) != len(As):
+        raise ValueError("A_list and B lists differ in length")
+    for i, a in enumerate(As):
+        _mat(a, f"A[{i}]")
+    for i, b in enumerate(Bs):
+        _mat(b, f"B[{i}]")
+    n = As[0].shape[0]
+    lda, ldb = As[0].stride(0), Bs[0].stride(0)
+    if any(a.stride(0) != lda or a.shape != (n, n) for a in As) or any(b.stride(0) != ldb for b in Bs):
+        raise ValueError("all A (and all B) must share shape and leading dimension")
+    dev = As[0].device
+    h = _handle(dev)
+    nprob = len(As)
+    o = default_opts(keep_all_X=1 if keep_all_X else 0, **opts)
+    if not isinstance(B, (list, tuple)):
+        o.b_fixed = 1
+    Lam = torch.empty((nprob, nev), dtype=torch.float64, device=dev)
+    res = torch.empty((nprob, nev), dtype=torch.float64, device=dev)
+    X = torch.empty(((nprob, n, nev) if keep_all_X else (n, nev)), dtype=torch.complex128, device=dev)
+    Ap = (C.c_void_p * nprob)(*[a.data_ptr() for a in As])
+    Bp = (C.c_void_p * nprob)(*[b.data_ptr() for b in Bs])
+    stats = (GevpStats * nprob)()
+    kprev, ldxp = 0, 0
+    if X_prev is not None:
+        _mat(X_prev, "X_prev")
+        kprev, ldxp = X_prev.shape[1], X_prev.stride(0)
+    st = load().gevp_solve_sequence(h, nprob, n, Ap, lda, Bp, ldb, nev, _ptr(X_prev), ldxp, kprev, C.byref(o),
+                                    _ptr(Lam), _ptr(X), nev, _ptr(res), stats)
+    if check and st not in (0, 3):
+        _check(st, h)
+    return SequenceResult(Lam, X, res, [s.as_dict() for s in stats], st)
+
+
+def chebyshev_filter(Cm: torch.Tensor, Y: torch.Tensor, degree: int, lo: float, hi: float, s: float,
+                     prec: str = "fp64") -> torch.Tensor:
+    """Y <- p(C) Y in place (scaled Chebyshev filter); returns Y."""
+    _mat(Cm, "C"); _mat(Y, "Y")
+    h = _handle(Cm.device)
+    st = load().gevp_chebyshev_filter(h, Cm.shape[0], _ptr(Cm), Cm.stride(0), _ptr(Y), Y.stride(0), Y.shape[1],
+                                      int(degree), float(lo), float(hi), float(s), PREC[prec])
+    _check(st, h)
+    return Y
+
+
+def cholqr2(Y: torch.Tensor, want_R: bool = False):
+    """Q (in place in Y) and optionally R with Y_in = Q R."""
+    _mat(Y, "Y")
+    h = _handle(Y.device)
+    m = Y.shape[1]
+    R = torch.zeros((m, m), dtype=torch.complex128, device=Y.device) if want_R else None
+    st = load().gevp_cholqr2(h, Y.shape[0], m, _ptr(Y), Y.stride(0), _ptr(R), m if want_R else 0)
+    _check(st, h)
+    return (Y, R) if want_R else Y
+
+
+def rayleigh_ritz(Cm: torch.Tensor, Q: torch.Tensor):
+    """(theta, Q <- Q Z in place, W = C Q, res)."""
+    _mat(Cm, "C"); _mat(Q, "Q")
+    h = _handle(Q.device)
+    n, m = Q.shape
+    W = torch.empty_like(Q)
+    th = torch.empty(m, dtype=torch.float64, device=Q.device)
+    rs = torch.empty(m, dtype=torch.float64, device=Q.device)
+    st = load().gevp_rayleigh_ritz(h, n, m, _ptr(Cm), Cm.stride(0), _ptr(Q), Q.stride(0), _ptr(W), m, _ptr(th),
+                                   _ptr(rs))
+    _check(st, h)
+    return th, Q, W, rs
+
+
+def heev_small(G: torch.Tensor):
+    _mat(G, "G")
+    h = _handle(G.device)
+    m = G.shape[0]
+    th = torch.empty(m, dtype=torch.float64, device=G.device)
+    Z = torch.empty_like(G)
+    st = load().gevp_heev_small(h, m, _ptr(G), G.stride(0), _ptr(th), _ptr(Z), m)
+    _check(st, h)
+    return th, Z
+
+
+def spectral_bounds(Cm: torch.Tensor, k: int = 32, count: int = 0):
+    _mat(Cm, "C")
+    h = _handle(Cm.device)
+    out = (C.c_double * 5)()
+    st = load().gevp_spectral_bounds(h, Cm.shape[0], _ptr(Cm), Cm.stride(0), int(k), int(count), out)
+    _check(st, h)
+    return list(out)
+
+
+def energy_backward(X: torch.Tensor, Lambda: torch.Tensor, gE: float = 1.0):
+    """(GA, GB) = (gE X X^H, -gE X diag(Lambda) X^H)."""
+    _mat(X, "X")
+    _mat(Lambda, "Lambda", torch.float64)
+    h = _handle(X.device)
+    n, nev = X.shape
+    GA = torch.empty((n, n), dtype=torch.complex128, device=X.device)
+    GB = torch.empty_like(GA)
+    st = load().gevp_energy_backward(h, n, nev, _ptr(X), X.stride(0), _ptr(Lambda.contiguous()), float(gE),
+                                     _ptr(GA), _ptr(GB), n)
+    _check(st, h)
+    return GA, GB
+
+
+def probe_peaks(device=None) -> dict:
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    h = _handle(dev)
+    out = (C.c_double * 3)()
+    st = load().gevp_probe_peaks(h, out)
+    _check(st, h)
+    return {"fp64_fma_tflops": out[0], "fp64_dmma_tflops": out[1], "fp32_fma_tflops": out[2]}
+
+
+def kernel_launches(device=None) -> int:
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    return int(load().gevp_kernel_launches(_handle(dev)))
+
+
+class GevpEnergy(torch.autograd.Function):
+    """E = sum of the lowest nev eigenvalues of A x = lambda B x, differentiable in A and B.
+
+    backward: dE/dA = X X^H, dE/dB = -X Lambda X^H (first-order perturbation theory for a
+    B-orthonormal X), computed by the library's backward kernel. For complex inputs torch
+    expects the conjugate Wirtinger gradient; for Hermitian perturbations the real-valued
+    directional derivative is Re tr(G^H dA) with G = X X^H, which is what is returned.
+    """
+
+    @staticmethod
+    def forward(ctx, A, B, nev, opts):
+        r = solve_sequence([A], B, nev, **(opts or {}))
+        ctx.save_for_backward(r.X, r.Lambda[0])
+        ctx.result = r
+        return r.Lambda[0].sum()
+
+    @staticmethod
+    def backward(ctx, gE):
+        X, lam = ctx.saved_tensors
+        GA, GB = energy_backward(X, lam, float(gE))
+        return GA, GB, None, None
+
+
+def band_energy(A, B, nev, **opts):
+    return GevpEnergy.apply(A, B, nev, opts)

@@ -1,0 +1,145 @@
+"""Per-step parity of the CUDA kernels (through the C ABI) with the FP64 oracle's
+definitions, on seeded inputs spanning several tiles and ragged tails."""
+import numpy as np
+import pytest
+import torch
+
+from tests.conftest import crandn, rand_herm, rand_hpd
+
+pytestmark = pytest.mark.gpu
+
+
+def T(x, dev):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 64, 127, 200])
+def test_reduce_parity(cuda, orc, n):
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(100 + n)
+    A, B = rand_herm(rng, n), rand_hpd(rng, n, 1e3)
+    L, C = gevp.reduce(T(A, cuda), T(B, cuda))
+    Lr, info = orc.potrf(B)
+    assert info == 0
+    Cr = orc.reduce(A, Lr)
+    assert relmax(L.cpu().numpy(), Lr) < 1e-13
+    assert relmax(C.cpu().numpy(), Cr) < 1e-12
+    assert np.array_equal(np.triu(L.cpu().numpy(), 1), np.zeros((n, n)))
+
+
+def test_reduce_not_hpd(cuda):
+    from paper_1007_4400_gb300 import gevp
+    B = np.diag(np.array([1.0, 2.0, -1.0, 3.0] + [1.0] * 60)).astype(np.complex128)
+    A = np.eye(64, dtype=np.complex128)
+    with pytest.raises(gevp.GevpError) as e:
+        gevp.reduce(T(A, cuda), T(B, cuda))
+    assert e.value.status == 2 and "pivot 3" in str(e.value)
+
+
+@pytest.mark.parametrize("n,m,deg", [(200, 13, 1), (200, 13, 2), (333, 40, 9), (64, 64, 5)])
+def test_filter_parity(cuda, orc, n, m, deg):
+    from oracle import pieces
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(200 + n + m + deg)
+    lam = np.sort(rng.uniform(-2, 50, n))
+    Q, _ = np.linalg.qr(crandn(rng, n, n))
+    Cm = (Q * lam) @ Q.conj().T
+    Cm = 0.5 * (Cm + Cm.conj().T)
+    Y0 = crandn(rng, n, m)
+    lo, hi, s = 5.0, 50.5, -2.5
+    Yg = gevp.chebyshev_filter(T(Cm, cuda), T(Y0, cuda), deg, lo, hi, s).cpu().numpy()
+    Yr = pieces.chebyshev_filter(Cm, Y0, deg, lo, hi, s)
+    assert relmax(Yg, Yr) < 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(300, 21), (1000, 48), (517, 140)])
+def test_cholqr2_parity(cuda, orc, n, m):
+    from oracle import pieces
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(300 + m)
+    Y = crandn(rng, n, m) @ np.diag(np.logspace(0, 3, m))
+    Qg, Rg = gevp.cholqr2(T(Y, cuda), want_R=True)
+    Qg, Rg = Qg.cpu().numpy(), Rg.cpu().numpy()
+    Qr, Rr = pieces.cholqr2(Y)
+    assert np.abs(Qg.conj().T @ Qg - np.eye(m)).max() < 1e-13
+    assert relmax(Qg, Qr) < 1e-10
+    assert relmax(Rg, Rr) < 1e-10
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 17, 64, 140, 200])
+def test_heev_small_parity(cuda, orc, m):
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(400 + m)
+    G = rand_herm(rng, m) * 10
+    th, Z = gevp.heev_small(T(G, cuda))
+    th, Z = th.cpu().numpy(), Z.cpu().numpy()
+    w, V = orc.heev(G, method="jacobi")
+    scale = np.abs(w).max()
+    assert np.abs(th - w).max() <= 1e-12 * scale
+    assert np.abs(Z.conj().T @ Z - np.eye(m)).max() < 1e-13
+    assert np.abs(G @ Z - Z * th).max() <= 1e-12 * scale
+
+
+def test_heev_small_degenerate(cuda, orc):
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(41)
+    m = 50
+    lam = np.concatenate([[-3.0], [1.0] * 3, np.linspace(2, 9, m - 4)])
+    Q, _ = np.linalg.qr(crandn(rng, m, m))
+    G = (Q * lam) @ Q.conj().T
+    G = 0.5 * (G + G.conj().T)
+    th, Z = gevp.heev_small(T(G, cuda))
+    th, Z = th.cpu().numpy(), Z.cpu().numpy()
+    assert np.abs(th - lam).max() < 1e-12 * 9
+    P1 = Q[:, 1:4] @ Q[:, 1:4].conj().T
+    P2 = Z[:, 1:4] @ Z[:, 1:4].conj().T
+    assert np.abs(P1 - P2).max() < 1e-10
+
+
+@pytest.mark.parametrize("n,m", [(256, 24), (611, 48)])
+def test_rayleigh_ritz_parity(cuda, orc, n, m):
+    from oracle import pieces
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(500 + n)
+    lam = np.sort(rng.uniform(-2, 50, n))
+    Qf, _ = np.linalg.qr(crandn(rng, n, n))
+    Cm = (Qf * lam) @ Qf.conj().T
+    Cm = 0.5 * (Cm + Cm.conj().T)
+    Q0, _ = np.linalg.qr(Qf[:, :m] + 1e-3 * crandn(rng, n, m))
+    th, Qg, Wg, rs = gevp.rayleigh_ritz(T(Cm, cuda), T(Q0, cuda))
+    thr, Qr, Wr = pieces.rayleigh_ritz(Cm, Q0)
+    assert np.abs(th.cpu().numpy() - thr).max() <= 1e-12 * 50
+    ov = np.abs(np.sum(np.conj(Qr) * Qg.cpu().numpy(), axis=0))
+    assert np.all(ov > 1 - 1e-9)
+    rr = pieces.residual_norms(Wr, Qr, thr)
+    assert np.abs(rs.cpu().numpy() - rr).max() <= 1e-11 * 50
+
+
+def test_spectral_bounds(cuda, orc):
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(600)
+    n = 500
+    lam = np.sort(rng.uniform(-2, 50, n))
+    Q, _ = np.linalg.qr(crandn(rng, n, n))
+    Cm = (Q * lam) @ Q.conj().T
+    Cm = 0.5 * (Cm + Cm.conj().T)
+    lo_ritz, hi_ritz, upper, aest, beta = gevp.spectral_bounds(T(Cm, cuda), 32, 48)
+    assert upper >= lam[-1]
+    assert lo_ritz >= lam[0] - 1e-4 * 50 and hi_ritz <= lam[-1] + 1e-4 * 50
+    assert lam[0] - 1 <= aest <= lam[-1] + 1
+
+
+@pytest.mark.parametrize("n,nev", [(100, 7), (300, 40)])
+def test_energy_backward_parity(cuda, orc, n, nev):
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(700 + n)
+    X = crandn(rng, n, nev)
+    lam = np.sort(rng.uniform(-2, 5, nev))
+    GA, GB = gevp.energy_backward(T(X, cuda), T(lam, cuda), 0.7)
+    GAr, GBr = orc.energy_grad(X, lam, 0.7)
+    assert relmax(GA.cpu().numpy(), GAr) < 1e-13
+    assert relmax(GB.cpu().numpy(), GBr) < 1e-13
