@@ -55,7 +55,8 @@ typedef enum {
 /* Precision of the Chebyshev filter (everything else is FP64). */
 typedef enum {
   GEVP_PREC_FP64 = 0,   /* FP64 complex GEMM                                           */
-  GEVP_PREC_FP32 = 1,   /* FP32-class: split-BF16 (hi+lo) planar operands on tcgen05    */
+  GEVP_PREC_FP32 = 1,   /* FP32-class: each operand split in three BF16 pieces, the six */
+                        /* significant cross products on tcgen05, FP32 accumulation     */
   GEVP_PREC_BF16 = 2    /* BF16 planar operands, 3-product (Gauss) complex GEMM on      */
                         /* tcgen05 tensor cores, FP32 accumulation in TMEM              */
 } gevp_prec;
@@ -86,12 +87,13 @@ typedef struct {
   double flops_fp64;    /* executed-flop model, FP64 work                               */
   double flops_lowp;    /* executed-flop model, tensor-core filter work (complex, 8/MAC) */
   double max_resid;
+  double orth_err;      /* max |Q^H Q - I| of the returned block (B-orthonormality of X)  */
   float ms_chol, ms_reduce, ms_bounds, ms_filter, ms_orth, ms_rr, ms_resid, ms_final, ms_total;
 } gevp_stats;
 
 /* Fills *o with the defaults: FP64 filter, tol 1e-10, max_outer 60, degrees 4..24,
  * nex 0 (callers set it), seed 10074400, b_fixed 0, cold_start 0, lanczos_steps 32,
- * refine_iters 2, keep_all_X 0. */
+ * refine_iters 3, keep_all_X 0. */
 void gevp_default_opts(gevp_opts* o);
 
 /* Creates a handle on CUDA device `device` bound to `stream` (a cudaStream_t; NULL =
@@ -144,6 +146,13 @@ gevp_status gevp_solve_sequence_host(gevp_handle h, int nprob, int64_t n, const 
  * prec: gevp_prec of the products. */
 gevp_status gevp_chebyshev_filter(gevp_handle h, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy,
                                   int m, int degree, double lo, double hi, double s, int prec);
+
+/* The filter's contraction alone on the tensor cores: D = C Y (n x n times n x m) with
+ * C and Y rounded to BF16 planes (real, imaginary, real + imaginary), the complex product
+ * formed from three real products (Gauss) with FP32 accumulation, D written in FP64.
+ * GEVP_ERR_UNSUPPORTED on devices other than sm_103. */
+gevp_status gevp_matmul_tc(gevp_handle h, int64_t n, int m, const void* C, int64_t ldc, const void* Y, int64_t ldy,
+                           void* D, int64_t ldd);
 
 /* CholQR2 (Fukaya, Nakatsukasa, Yanagisawa & Yamamoto 2014): Y (n x m) <- Q with
  * Q^H Q = I and Y_in = Q R, R upper triangular with positive diagonal (written to R,

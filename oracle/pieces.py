@@ -109,7 +109,9 @@ def lanczos_upper_bound_ok(Cm, b: float) -> bool:
 
 def principal_sines(X1, X2, B=None):
     """Sines of the principal angles between span(X1) and span(X2) in the B inner
-    product (B = I if None): the paper's subspace deviation angle applied to clusters."""
+    product (B = I if None): the paper's subspace deviation angle applied to clusters.
+    Computed as the singular values of (I - Q2 Q2^H) Q1, which stays accurate for small
+    angles (unlike sqrt(1 - cos^2))."""
     X1 = np.asarray(X1, dtype=np.complex128)
     X2 = np.asarray(X2, dtype=np.complex128)
     if B is not None:
@@ -120,9 +122,9 @@ def principal_sines(X1, X2, B=None):
         X2 = Lb.conj().T @ X2
     q1, _ = np.linalg.qr(X1)
     q2, _ = np.linalg.qr(X2)
-    s = np.linalg.svd(q1.conj().T @ q2, compute_uv=False)
-    s = np.clip(s, 0.0, 1.0)
-    return np.sqrt(np.maximum(0.0, 1.0 - s ** 2))
+    D = q1 - q2 @ (q2.conj().T @ q1)
+    s = np.linalg.svd(D, compute_uv=False)
+    return np.clip(s, 0.0, 1.0)
 
 
 def deviation_angles(X_old, X_new, B):

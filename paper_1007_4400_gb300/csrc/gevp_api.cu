@@ -279,58 +279,71 @@ void reduce_into(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, double2*
 }
 
 // Orthonormalise Y (n x ma, ld ldy) against Q[:, 0:nlock] and by CholQR2; result in Out.
+// A pass whose Gram matrix is not numerically positive definite is repeated as shifted
+// CholQR (Fukaya et al. 2020); the result is accepted only after two consecutive plain
+// passes (so a shifted pass is always followed by CholQR2). A block that stays rank
+// deficient is replaced by fresh random columns (projected against the locked ones).
 gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_t ldy, int ma, double2* Out,
-                           int64_t ldo, gevp_stats* st) {
+                           int64_t ldo, gevp_stats* st, uint64_t seed = 0) {
   const int64_t ldq = h->cap_m;
-  for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
-    ZgemmArgs p = zg(nlock, ma, (int)n, h->Q, ldq, 1, Y, ldy, 0, h->P, ma);
-    zgemm(p, h->split, h->split_elems, h->stream);
-    ZgemmArgs u = zg((int)n, ma, nlock, h->Q, ldq, 0, h->P, ma, 0, Y, ldy, -1.0);
-    u.Cin = Y; u.ldc = ldy; u.beta = 1.0;
-    zgemm(u, h->split, h->split_elems, h->stream);
-  }
-  double2* src = Y;
-  int64_t lds = ldy;
-  double2* dst = Out;
-  int64_t ldd = ldo;
-  for (int pass = 0; pass < 2; ++pass) {
-    bool shifted = false;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-      ZgemmArgs g = zg(ma, ma, (int)n, src, lds, 1, src, lds, 0, h->Gw, ma);
-      g.triD = 1;
-      zgemm(g, h->split, h->split_elems, h->stream);
-      hermitize_lower(ma, h->Gw, ma, h->stream);
-      gram_scale(ma, h->Gw, ma, h->dscale, h->stream);
-      if (shifted) {
-        // shifted CholQR (Fukaya et al. 2020): s = 11 (n m + m (m+1)) u ||Y D||_2^2, ||Y D||_F^2 = m
-        double u = 1.1102230246251565e-16;
-        double sh = 11.0 * ((double)n * ma + (double)ma * (ma + 1)) * u * ma * std::pow(10.0, attempt - 1);
-        zshift_diag(ma, h->Gw, ma, sh, h->stream);
-      }
-      CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
-      potrf_lower(ma, h->Gw, ma, h->info, nullptr, 0, h->stream);
-      int info = 0;
-      TRY(sync_read(h, h->info, &info, sizeof(int)));
-      if (info == 0) break;
-      if (attempt == 2) {
-        h->err = "CholQR: Gram matrix not positive definite after shifting";
-        return GEVP_ERR_NOT_HPD;
-      }
-      shifted = true;
-      if (st) st->orth_fallbacks++;
+  for (int restart = 0; restart < 2; ++restart) {
+    for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
+      ZgemmArgs p = zg(nlock, ma, (int)n, h->Q, ldq, 1, Y, ldy, 0, h->P, ma);
+      zgemm(p, h->split, h->split_elems, h->stream);
+      ZgemmArgs u = zg((int)n, ma, nlock, h->Q, ldq, 0, h->P, ma, 0, Y, ldy, -1.0);
+      u.Cin = Y; u.ldc = ldy; u.beta = 1.0;
+      zgemm(u, h->split, h->split_elems, h->stream);
     }
-    trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream);
-    zcol_scale(n, ma, src, lds, h->dscale, h->stream);
-    ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
-    q.triB = 2;
-    zgemm(q, h->split, h->split_elems, h->stream);
-    if (st) st->flops_fp64 += 8.0 * (double)n * ma * ma * 1.5;
-    std::swap(src, dst);
-    std::swap(lds, ldd);
+    double2* src = Y;
+    int64_t lds = ldy;
+    double2* dst = Out;
+    int64_t ldd = ldo;
+    int plain_ok = 0;
+    bool failed = false;
+    for (int pass = 0; pass < 6 && plain_ok < 2; ++pass) {
+      bool shifted = false;
+      int attempt = 0;
+      for (; attempt < 3; ++attempt) {
+        ZgemmArgs g = zg(ma, ma, (int)n, src, lds, 1, src, lds, 0, h->Gw, ma);
+        g.triD = 1;
+        zgemm(g, h->split, h->split_elems, h->stream);
+        hermitize_lower(ma, h->Gw, ma, h->stream);
+        gram_scale(ma, h->Gw, ma, h->dscale, h->stream);
+        if (shifted) {
+          // s = 11 (n m + m (m+1)) u ||Y D||_2^2 with ||Y D||_F^2 = m, grown 100x per retry
+          double u = 1.1102230246251565e-16;
+          double sh = 11.0 * ((double)n * ma + (double)ma * (ma + 1)) * u * ma * std::pow(100.0, attempt - 1);
+          zshift_diag(ma, h->Gw, ma, sh, h->stream);
+        }
+        CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
+        potrf_lower(ma, h->Gw, ma, h->info, nullptr, 0, h->stream);
+        int info = 0;
+        TRY(sync_read(h, h->info, &info, sizeof(int)));
+        if (info == 0) break;
+        shifted = true;
+        if (st) st->orth_fallbacks++;
+      }
+      if (attempt == 3) { failed = true; break; }
+      plain_ok = shifted ? 0 : plain_ok + 1;
+      trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream);
+      zcol_scale(n, ma, src, lds, h->dscale, h->stream);
+      ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
+      q.triB = 2;
+      zgemm(q, h->split, h->split_elems, h->stream);
+      if (st) st->flops_fp64 += 8.0 * (double)n * ma * ma * 1.5;
+      std::swap(src, dst);
+      std::swap(lds, ldd);
+    }
+    if (!failed && plain_ok >= 2) {
+      if (src != Out) zcopy2d(n, ma, src, lds, Out, ldo, h->stream);
+      return GEVP_OK;
+    }
+    // rank deficient: restart the block from random columns
+    zrandn(n, ma, Y, ldy, 0x9E3779B97F4A7C15ull ^ (seed + 7919ull * (uint64_t)(restart + 1)), h->stream);
+    if (st) st->orth_fallbacks += 100;
   }
-  // after two passes the result is back in Y's buffer (src); copy to Out
-  if (src != Out) zcopy2d(n, ma, src, lds, Out, ldo, h->stream);
-  return GEVP_OK;
+  h->err = "CholQR: block stays rank deficient";
+  return GEVP_ERR_NOT_HPD;
 }
 
 // Rayleigh-Ritz on the active columns Q[:, nlock:nlock+ma]; updates Q, W, theta, res there.
@@ -433,12 +446,20 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   S.normC = std::max(std::fabs(hb[0]), std::fabs(hb[2]));
   TRY(lanczos(h, n, A, lda, o.lanczos_steps, 0, o.seed + 104729ull * prob_index + 1, hb));
   S.normA = std::max(std::fabs(hb[0]), std::fabs(hb[1]));
+  int prec = o.filter_prec;
+  const int nsplit = (prec == GEVP_PREC_FP32) ? 3 : 1;
+  if (prec != GEVP_PREC_FP64) {
+    CK(filter_tc_reserve(&h->tc, n, m));
+    CK(filter_tc_set_matrix(h->tc, n, h->C, n, nsplit, h->stream));
+  }
   tm.mark(PH_BOUNDS);
   if (!warm) {
     zrandn(n, m, h->Y1, ld, o.seed * 1000003ull + (uint64_t)prob_index, h->stream);
     TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
     tm.mark(PH_ORTH);
-  } else {
+  }
+  if (warm || m == n) {
+    // warm start, or a block that spans the whole space (then this projection is exact)
     TRY(rayleigh_ritz(h, n, 0, m, h->C, n, o.refine_iters, st));
     TRY(sync_read(h, h->theta, S.theta.data(), m * sizeof(double)));
     TRY(sync_read(h, h->res, S.res.data(), m * sizeof(double)));
@@ -448,7 +469,6 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   double tolC = 0.1 * o.tol * S.normC;
   int final_pass = 0;
   double prev_maxres = 1e300;
-  int prec = o.filter_prec;
   bool converged = false;
   for (int it = 0;; ++it) {
     if (S.have_theta) {
@@ -482,6 +502,7 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
       // tighten the C-space tolerance and re-open the failing pairs
       tolC *= 0.05;
       S.nlock = first_bad;
+      if (prec != GEVP_PREC_FP64 && st) st->switches++;
       prec = GEVP_PREC_FP64;
       continue;
     }
@@ -494,14 +515,30 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     if (!(lo > sc + 1e-3 * (hi - sc))) lo = sc + 0.5 * (hi - sc);
     if (!(hi > lo)) hi = lo + 1e-3 * S.normC + 1e-300;
     int deg = S.have_theta ? choose_degree(S, lo, hi, tolC, o.deg_min, o.deg_max) : std::min(o.deg_max, 10);
-    double2* Yf = filter_fp64(h, n, h->C, n, h->Q + S.nlock, ld, ma, deg, lo, hi, sc, h->Y1, h->Y2, ld);
+    double2* Yf;
+    if (prec != GEVP_PREC_FP64) {
+      if (S.have_theta) {
+        // residual-corrected: the tensor cores filter the defect driven by R = W - Q Theta
+        CK(filter_tc_apply_corrected(h->tc, n, ma, h->Q + S.nlock, ld, h->W + S.nlock, ld, h->theta + S.nlock,
+                                     S.theta.data() + S.nlock, h->Y1, ld, deg, lo, hi, sc, nsplit,
+                                     h->stream));
+        if (st) st->flops_lowp += 8.0 * (double)n * n * ma * (deg - 1);
+      } else {
+        CK(filter_tc_apply(h->tc, n, ma, h->Q + S.nlock, ld, h->Y1, ld, deg, lo, hi, sc, nsplit, nullptr,
+                           h->stream));
+        if (st) st->flops_lowp += 8.0 * (double)n * n * ma * deg;
+      }
+      Yf = h->Y1;
+    } else {
+      Yf = filter_fp64(h, n, h->C, n, h->Q + S.nlock, ld, ma, deg, lo, hi, sc, h->Y1, h->Y2, ld);
+      if (st) st->flops_fp64 += 8.0 * (double)n * n * ma * deg;
+    }
     if (st) {
       st->filter_steps += deg;
       st->matvecs += (int64_t)deg * ma;
-      st->flops_fp64 += 8.0 * (double)n * n * ma * deg;
     }
     tm.mark(PH_FILTER);
-    TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st));
+    TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st, o.seed + 31ull * it + 7ull * prob_index));
     tm.mark(PH_ORTH);
     TRY(rayleigh_ritz(h, n, S.nlock, ma, h->C, n, o.refine_iters, st));
     TRY(sync_read(h, h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double)));
@@ -511,10 +548,26 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     if (st) st->outer_iters++;
     double mr = 0;
     for (int i = S.nlock; i < nev; ++i) mr = std::max(mr, S.res[i]);
+    // precision switch: the low-precision filter has stalled (less than 4x progress in a
+    // round) or the residuals reached its floor -> FP64 for the rest of this problem
+    if (prec != GEVP_PREC_FP64 && mr > 0.25 * prev_maxres) {
+      prec = GEVP_PREC_FP64;
+      if (st) st->switches++;
+    }
     prev_maxres = mr;
   }
-  (void)prev_maxres;
-  (void)prec;
+  if (st) {
+    // ||Q^H Q - I||_max over the returned block (= ||X^H B X - I|| up to the rounding of L^-1)
+    zset_identity(nev, nev, h->Gwi, nev, h->stream);
+    ZgemmArgs g = zg(nev, nev, (int)n, h->Q, ld, 1, h->Q, ld, 0, h->Gwi, nev, -1.0);
+    g.Cin = h->Gwi; g.ldc = nev; g.beta = 1.0;
+    zgemm(g, h->split, h->split_elems, h->stream);
+    std::vector<double2> gg((size_t)nev * nev);
+    TRY(sync_read(h, h->Gwi, gg.data(), gg.size() * sizeof(double2)));
+    double mx = 0;
+    for (auto& v : gg) mx = std::max(mx, std::sqrt(v.x * v.x + v.y * v.y));
+    st->orth_err = mx;
+  }
   CK(cudaMemcpyAsync(Lam_out, h->lam, nev * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemcpyAsync(res_out, h->resf, nev * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (X_out) zcopy2d(n, nev, h->Xf, ld, X_out, ldx, h->stream);
@@ -542,7 +595,7 @@ void gevp_default_opts(gevp_opts* o) {
   o->b_fixed = 0;
   o->cold_start = 0;
   o->lanczos_steps = 32;
-  o->refine_iters = 2;
+  o->refine_iters = 3;
   o->keep_all_X = 0;
 }
 
@@ -577,6 +630,7 @@ gevp_status gevp_destroy(gevp_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->tc) gevp::filter_tc_release(h->tc);
   if (h->arena) cudaFree(h->arena);
   if (h->hbuf) cudaFreeHost(h->hbuf);
   for (auto e : h->evpool) cudaEventDestroy(e);
@@ -626,6 +680,11 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
   if (X_prev && (kprev < 1 || kprev > m || bad_ld(ldxp, kprev))) return GEVP_ERR_INVALID_ARG;
   if (m > 1024) { h->err = "block width nev + nex above 1024"; return GEVP_ERR_UNSUPPORTED; }
   if (o.refine_iters < 1) o.refine_iters = 1;
+  if (o.filter_prec < 0 || o.filter_prec > 2) return GEVP_ERR_INVALID_ARG;
+  if (o.filter_prec != GEVP_PREC_FP64 && !tc_filter_supported()) {
+    h->err = "tensor-core filter needs an sm_103 device";
+    return GEVP_ERR_UNSUPPORTED;
+  }
   if (o.deg_min < 1) o.deg_min = 1;
   if (o.deg_max < o.deg_min) o.deg_max = o.deg_min;
   if (o.lanczos_steps < 4) o.lanczos_steps = 4;
@@ -735,15 +794,44 @@ gevp_status gevp_chebyshev_filter(gevp_handle h, int64_t n, const void* C, int64
   if (!h || n < 0 || m < 0 || degree < 1 || !(hi > lo) || !(lo > s)) return GEVP_ERR_INVALID_ARG;
   if (n == 0 || m == 0) return GEVP_OK;
   if (!C || !Y || bad_ld(ldc, n) || bad_ld(ldy, m)) return GEVP_ERR_INVALID_ARG;
-  if (prec != GEVP_PREC_FP64) return GEVP_ERR_UNSUPPORTED;
+  if (prec < 0 || prec > 2) return GEVP_ERR_UNSUPPORTED;
   cudaSetDevice(h->device);
   TRY(ensure(h, n, m));
   const int64_t ld = h->cap_m;
+  if (prec != GEVP_PREC_FP64) {
+    if (!tc_filter_supported()) return GEVP_ERR_UNSUPPORTED;
+    const int nsplit = (prec == GEVP_PREC_FP32) ? 3 : 1;
+    CK(filter_tc_reserve(&h->tc, n, m));
+    CK(filter_tc_set_matrix(h->tc, n, (const double2*)C, ldc, nsplit, h->stream));
+    int err = 0;
+    CK(filter_tc_apply(h->tc, n, m, (const double2*)Y, ldy, (double2*)Y, ldy, degree, lo, hi, s, nsplit, &err,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (err) { h->err = "tensor-core filter: a bounded wait expired"; return GEVP_ERR_TIMEOUT; }
+    return GEVP_OK;
+  }
   double2* out = filter_fp64(h, n, (const double2*)C, ldc, (const double2*)Y, ldy, m, degree, lo, hi, s, h->Y1,
                              h->Y2, ld);
   zcopy2d(n, m, out, ld, (double2*)Y, ldy, h->stream);
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_matmul_tc(gevp_handle h, int64_t n, int m, const void* C, int64_t ldc, const void* Y, int64_t ldy,
+                           void* D, int64_t ldd) {
+  if (!h || n < 0 || m < 0) return GEVP_ERR_INVALID_ARG;
+  if (n == 0 || m == 0) return GEVP_OK;
+  if (!C || !Y || !D || bad_ld(ldc, n) || bad_ld(ldy, m) || bad_ld(ldd, m)) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  if (!tc_filter_supported()) return GEVP_ERR_UNSUPPORTED;
+  CK(filter_tc_reserve(&h->tc, n, m));
+  CK(filter_tc_set_matrix(h->tc, n, (const double2*)C, ldc, 1, h->stream));
+  int err = 0;
+  CK(filter_tc_product(h->tc, n, m, (const double2*)Y, ldy, (double2*)D, ldd, 1, &err, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (err) { h->err = "tensor-core product: a bounded wait expired"; return GEVP_ERR_TIMEOUT; }
   return GEVP_OK;
 }
 
@@ -781,7 +869,7 @@ gevp_status gevp_rayleigh_ritz(gevp_handle h, int64_t n, int m, const void* C, i
   const int64_t ld = h->cap_m;
   h->have_prev = false;
   zcopy2d(n, m, (const double2*)Q, ldq, h->Q, ld, h->stream);
-  TRY(rayleigh_ritz(h, n, 0, m, (const double2*)C, ldc, 2, nullptr));
+  TRY(rayleigh_ritz(h, n, 0, m, (const double2*)C, ldc, 3, nullptr));
   zcopy2d(n, m, h->Q, ld, (double2*)Q, ldq, h->stream);
   zcopy2d(n, m, h->W, ld, (double2*)W, ldw, h->stream);
   CK(cudaMemcpyAsync(theta, h->theta, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -797,7 +885,7 @@ gevp_status gevp_heev_small(gevp_handle h, int m, const void* G, int64_t ldg, do
   if (!G || !theta || !Z || bad_ld(ldg, m) || bad_ld(ldz, m)) return GEVP_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   TRY(ensure(h, std::max<int64_t>(m, h->cap_n), m));
-  heev_small(m, (const double2*)G, ldg, theta, (double2*)Z, ldz, h->hw, 2, h->stream);
+  heev_small(m, (const double2*)G, ldg, theta, (double2*)Z, ldz, h->hw, 3, h->stream);
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return GEVP_OK;

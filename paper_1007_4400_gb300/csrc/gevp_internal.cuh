@@ -134,6 +134,19 @@ void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const
 // ---------------------------------------------------------------- low-precision filter (tcgen05)
 struct FilterTC;   // opaque, owned by the handle
 bool tc_filter_supported();
+cudaError_t filter_tc_reserve(FilterTC** f, int64_t n, int m);
+void filter_tc_release(FilterTC* f);
+// nsplit: BF16 pieces per operand (1 = BF16 filter, 3 = FP32-class, see filter_tc.cu)
+cudaError_t filter_tc_set_matrix(FilterTC* f, int64_t n, const double2* C, int64_t ldc, int nsplit, cudaStream_t s);
+cudaError_t filter_tc_apply(FilterTC* f, int64_t n, int m, const double2* Y, int64_t ldy, double2* Yout,
+                            int64_t ldo, int deg, double lo, double hi, double sc, int nsplit, int* err_host,
+                            cudaStream_t s);
+cudaError_t filter_tc_apply_corrected(FilterTC* f, int64_t n, int m, const double2* Q, int64_t ldq, const double2* W,
+                                      int64_t ldw, const double* theta_dev, const double* theta_host, double2* Yout,
+                                      int64_t ldo, int deg, double lo, double hi, double sc, int nsplit,
+                                      cudaStream_t s);
+cudaError_t filter_tc_product(FilterTC* f, int64_t n, int m, const double2* Y, int64_t ldy, double2* D, int64_t ldd,
+                              int nsplit, int* err_host, cudaStream_t s);
 
 // ---------------------------------------------------------------- probes
 void probe_peaks(double* fp64_fma_tflops, double* fp64_dmma_tflops, double* fp32_fma_tflops, cudaStream_t s);

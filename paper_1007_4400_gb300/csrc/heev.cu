@@ -6,10 +6,16 @@
 //      clock per SM), giving eigenvectors accurate to about 1e-6;
 //   2. Ogita & Aishima's iterative refinement for symmetric/Hermitian eigenvector
 //      matrices (Japan J. Ind. Appl. Math. 35, 2018), which converges quadratically and
-//      consists of four FP64 GEMMs per step spread over all SMs; two steps reach FP64
-//      accuracy. Nearly coincident eigenvalues (closer than the refinement's delta) are
-//      treated as a cluster: their vectors stay an orthonormal basis of the cluster's
-//      invariant subspace, which is all the Rayleigh-Ritz step needs.
+//      consists of four FP64 GEMMs per step spread over all SMs. Pairs closer than the
+//      refinement's threshold, and pairs whose first-order correction would exceed 0.2,
+//      are left for later steps; the last step corrects only the orthonormality (a
+//      symmetric Newton-Schulz step);
+//   3. S = Z^H G Z in FP64 and exact FP64 Jacobi rotations, in one CTA, on the few pairs of
+//      S whose coupling is still above 1e-15 ||G||_F (near-degenerate clusters the
+//      refinement cannot separate); eigenvalues = diag(S).
+// FP32 Jacobi uses hypot for |g_pq| (the squares of tiny couplings are denormal and would
+// make the phase, hence the rotation, non-unitary) and skips couplings below FP32
+// significance relative to the diagonal.
 #include "gevp_internal.cuh"
 #include <algorithm>
 
@@ -59,7 +65,9 @@ __global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* 
   float fro2 = 0.f;
   for (int e = tid; e < m * m; e += JT) { float2 g = G[e]; fro2 += g.x * g.x + g.y * g.y; }
   fro2 = block_sum(fro2, red);
-  const float tol2 = 1e-13f * fro2;   // (3.2e-7 * ||G||_F)^2
+  // sweep until the off-diagonal norm reaches the FP32 noise level or stops falling
+  const float tol2 = 1e-16f * fro2;   // (1e-8 ||G||_F)^2
+  float off_prev = 3.0e38f;
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
     float off = 0.f;
@@ -68,7 +76,10 @@ __global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* 
       if (i != j) { float2 g = G[e]; off += g.x * g.x + g.y * g.y; }
     }
     off = block_sum(off, red);
-    if (off <= tol2) break;
+    // converged, or stagnated at the FP32 noise level (early sweeps on clustered spectra
+    // can reduce the off-norm slowly, so slow progress alone is not a reason to stop)
+    if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
+    off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
       for (int k = tid; k < npairs; k += JT) {
         int p, q;
@@ -78,9 +89,12 @@ __global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* 
         float4 u = make_float4(1.f, 0.f, 1.f, 0.f);
         if (q < m) {
           float2 apq = G[p * m + q];
-          float r = sqrtf(apq.x * apq.x + apq.y * apq.y);
-          if (r > 1e-30f) {
-            float app = G[p * m + p].x, aqq = G[q * m + q].x;
+          // |g_pq| without under/overflow: the phase g_pq / |g_pq| must stay unit-modulus
+          // or the rotation stops being unitary (squares of tiny off-diagonals are denormal)
+          float r = hypotf(apq.x, apq.y);
+          float app = G[p * m + p].x, aqq = G[q * m + q].x;
+          // skip couplings below FP32 significance relative to the diagonal
+          if (r > 1e-30f && r > 1e-10f * (fabsf(app) + fabsf(aqq))) {
             float tau = (aqq - app) / (2.f * r);
             float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             float c = rsqrtf(1.f + t * t);
@@ -201,19 +215,21 @@ __global__ void oa_scalars_kernel(int m, const double2* R, const double2* S, dou
 }
 
 __global__ void oa_update_kernel(int m, const double2* R, const double2* S, const double* lam, const double* scal,
-                                 double2* E) {
+                                 double2* E, int only_orth) {
   int64_t total = (int64_t)m * m;
-  double delta = scal[0];
+  double delta = only_orth ? 1e300 : scal[0];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / m), j = (int)(e % m);
     double2 r = R[e];
     double2 v;
     double d = lam[j] - lam[i];
+    v = zscale(r, 0.5);
     if (i != j && fabs(d) > delta) {
       double2 sv = S[e];
-      v = make_double2((sv.x + lam[j] * r.x) / d, (sv.y + lam[j] * r.y) / d);
-    } else {
-      v = zscale(r, 0.5);
+      double2 t = make_double2(sv.x + lam[j] * r.x, sv.y + lam[j] * r.y);
+      // first-order correction only where it is small (|E_ij| <= 0.2); larger couplings
+      // are left to the next step, which keeps the iteration from diverging
+      if (sqrt(zabs2(t)) <= 0.2 * fabs(d)) v = make_double2(t.x / d, t.y / d);
     }
     E[e] = v;
   }
@@ -225,6 +241,82 @@ __global__ void frob_kernel(int m, const double2* G, int64_t ldg, double* out) {
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) s += zabs2(G[(e / m) * ldg + (e % m)]);
   s = block_sum_d(s, red);
   if (threadIdx.x == 0) out[0] = sqrt(s);
+}
+
+// Clusters the refinement leaves mixed (pairs closer than its threshold): S = Z^H G Z is
+// diagonal apart from those couplings. One CTA finds the pairs with |s_pq| above tol and
+// applies exact FP64 Jacobi rotations to them (S two-sided, Z on the right), a few at a
+// time, for a few sweeps; typically a handful of rotations. lam <- diag(S).
+__global__ void __launch_bounds__(1024) cluster_jacobi_kernel(int m, double2* S, double2* Z, double* lam,
+                                                              const double* fro, double rel, int max_sweeps) {
+  const double tol = rel * fro[0];
+  constexpr int kMaxPairs = 256;
+  __shared__ int PI[kMaxPairs], PJ[kMaxPairs];
+  __shared__ int npairs;
+  __shared__ double2 ucs[3];   // c, s (real), ph
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) npairs = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = e / m, j = e % m;
+      if (j <= i) continue;
+      double2 v = S[e];
+      if (hypot(v.x, v.y) > tol) {
+        int k = atomicAdd(&npairs, 1);
+        if (k < kMaxPairs) { PI[k] = i; PJ[k] = j; }
+      }
+    }
+    __syncthreads();
+    int np = min(npairs, kMaxPairs);
+    if (np == 0) break;
+    for (int k = 0; k < np; ++k) {
+      int p = PI[k], q = PJ[k];
+      if (threadIdx.x == 0) {
+        double2 apq = S[p * m + q];
+        double r = hypot(apq.x, apq.y);
+        double c = 1.0, s = 0.0;
+        double2 ph = make_double2(1.0, 0.0);
+        if (r > 0.0) {
+          double app = S[p * m + p].x, aqq = S[q * m + q].x;
+          double tau = (aqq - app) / (2.0 * r);
+          double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+          ph = make_double2(apq.x / r, apq.y / r);
+        }
+        ucs[0] = make_double2(c, 0.0);
+        ucs[1] = make_double2(s, 0.0);
+        ucs[2] = ph;
+      }
+      __syncthreads();
+      const double c = ucs[0].x, s = ucs[1].x;
+      const double2 ph = ucs[2], phc = zconj(ph);
+      // columns p, q of S and Z: [x_p, x_q] <- [c x_p - s conj(ph) x_q, s x_p + c conj(ph) x_q]
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double2 a = S[i * m + p], b = zmul(S[i * m + q], phc);
+        S[i * m + p] = make_double2(c * a.x - s * b.x, c * a.y - s * b.y);
+        S[i * m + q] = make_double2(s * a.x + c * b.x, s * a.y + c * b.y);
+        double2 za = Z[i * m + p], zb = zmul(Z[i * m + q], phc);
+        Z[i * m + p] = make_double2(c * za.x - s * zb.x, c * za.y - s * zb.y);
+        Z[i * m + q] = make_double2(s * za.x + c * zb.x, s * za.y + c * zb.y);
+      }
+      __syncthreads();
+      // rows p, q of S: [r_p; r_q] <- [c r_p - s ph r_q; s r_p + c ph r_q]
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double2 a = S[p * m + j], b = zmul(ph, S[q * m + j]);
+        double2 np_ = make_double2(c * a.x - s * b.x, c * a.y - s * b.y);
+        double2 nq_ = make_double2(s * a.x + c * b.x, s * a.y + c * b.y);
+        if (j == q) np_ = make_double2(0.0, 0.0);
+        if (j == p) nq_ = make_double2(0.0, 0.0);
+        if (j == p) np_.y = 0.0;
+        if (j == q) nq_.y = 0.0;
+        S[p * m + j] = np_;
+        S[q * m + j] = nq_;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = S[i * m + i].x;
 }
 
 // final ordering: theta ascending, Z columns permuted accordingly
@@ -268,7 +360,7 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   int blocks = (int)std::min<int64_t>((mm + 255) / 256, 152 * 4);
   g_to_c_kernel<<<blocks, 256, 0, s>>>(m, G, ldg, w.G32);
   LAUNCH_NOTE(1);
-  jacobi32_kernel<<<1, JT, 0, s>>>(m, w.G32, w.Z32, w.w32, w.perm, 30);
+  jacobi32_kernel<<<1, JT, 0, s>>>(m, w.G32, w.Z32, w.w32, w.perm, 40);
   LAUNCH_NOTE(1);
   gather_z_kernel<<<blocks, 256, 0, s>>>(m, w.Z32, w.perm, w.Z, m);
   LAUNCH_NOTE(1);
@@ -276,7 +368,7 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   LAUNCH_NOTE(1);
   double2* Z = w.Z;
   double2* Zn = w.T;   // ping-pong partner
-  for (int it = 0; it < refine_iters; ++it) {
+  for (int it = 0; it <= refine_iters; ++it) {
     // R = I - Z^H Z
     zset_identity(m, m, w.R, m, s);
     ZgemmArgs a = zg(m, m, m, Z, m, 1, Z, m, 0, w.R, m, -1.0);
@@ -289,7 +381,9 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
     zgemm(c, w.split_ws, w.split_ws_elems, s);
     oa_scalars_kernel<<<1, 1024, 0, s>>>(m, w.R, w.S, w.lam, w.scal);
     LAUNCH_NOTE(1);
-    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E);
+    // the last step corrects only the orthonormality (E = R/2 everywhere: a symmetric
+    // Newton-Schulz step) and yields Rayleigh quotients of the vectors it returns
+    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, it == refine_iters ? 1 : 0);
     LAUNCH_NOTE(1);
     // Zn = Z + Z E
     ZgemmArgs d = zg(m, m, m, Z, m, 0, w.E, m, 0, Zn, m);
@@ -297,11 +391,15 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
     zgemm(d, w.split_ws, w.split_ws_elems, s);
     std::swap(Z, Zn);
   }
-  if (refine_iters == 0) {
-    // eigenvalues straight from the FP32 solve
-    // (theta written by the sort kernel from lam; fill lam from w32)
-    // convert on device via a tiny kernel: reuse sort on w32 cast
-  }
+  // resolve what the refinement left mixed: S = Z^H G Z, exact rotations on its remaining
+  // couplings (near-degenerate clusters), eigenvalues = diag(S)
+  ZgemmArgs b2 = zg(m, m, m, G, ldg, 0, Z, m, 0, w.E, m);
+  zgemm(b2, w.split_ws, w.split_ws_elems, s);
+  ZgemmArgs c2 = zg(m, m, m, Z, m, 1, w.E, m, 0, w.S, m);
+  zgemm(c2, w.split_ws, w.split_ws_elems, s);
+  hermitize_avg(m, w.S, m, s);
+  cluster_jacobi_kernel<<<1, 1024, 0, s>>>(m, w.S, Z, w.lam, w.scal + 1, 1e-15, 6);
+  LAUNCH_NOTE(1);
   sort_pairs_kernel<<<1, 1024, 0, s>>>(m, w.lam, Z, theta, Zout, ldz);
   LAUNCH_NOTE(1);
 }

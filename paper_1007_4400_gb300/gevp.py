@@ -43,7 +43,7 @@ class GevpStats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("filter_steps", C.c_int), ("switches", C.c_int),
                 ("orth_fallbacks", C.c_int), ("final_passes", C.c_int), ("converged", C.c_int),
                 ("matvecs", C.c_int64), ("flops_fp64", C.c_double), ("flops_lowp", C.c_double),
-                ("max_resid", C.c_double),
+                ("max_resid", C.c_double), ("orth_err", C.c_double),
                 ("ms_chol", C.c_float), ("ms_reduce", C.c_float), ("ms_bounds", C.c_float),
                 ("ms_filter", C.c_float), ("ms_orth", C.c_float), ("ms_rr", C.c_float), ("ms_resid", C.c_float),
                 ("ms_final", C.c_float), ("ms_total", C.c_float)]

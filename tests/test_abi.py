@@ -41,7 +41,7 @@ def test_host_only_calls_without_gpu():
     assert L.gevp_status_string(2) == b"GEVP_ERR_NOT_HPD"
     assert b"sm_103a" in L.gevp_version()
     o = gevp.default_opts()
-    assert o.tol == 1e-10 and o.refine_iters == 2
+    assert o.tol == 1e-10 and o.refine_iters == 3
     # a null handle is rejected, never dereferenced
     assert L.gevp_destroy(None) == 1
 

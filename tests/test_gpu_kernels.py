@@ -84,6 +84,25 @@ def test_heev_small_parity(cuda, orc, m):
     assert np.abs(G @ Z - Z * th).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("m", [48, 140, 300])
+def test_heev_small_clustered_wide(cuda, orc, m):
+    # the shape of a cold-start Rayleigh-Ritz projection: a dense cluster of small values,
+    # a near-degenerate pair and a wide sparse tail; Z must stay orthonormal to FP64 level
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(4200 + m)
+    k = int(0.7 * m)
+    lam = np.concatenate([np.sort(rng.uniform(-2, 2, k)), [3.0, 3.0 + 1e-9],
+                          np.sort(rng.uniform(5, 60, m - k - 2))])
+    Q, _ = np.linalg.qr(crandn(rng, m, m))
+    G = (Q * lam) @ Q.conj().T
+    G = 0.5 * (G + G.conj().T)
+    th, Z = gevp.heev_small(T(G, cuda))
+    th, Z = th.cpu().numpy(), Z.cpu().numpy()
+    assert np.abs(Z.conj().T @ Z - np.eye(m)).max() < 1e-13
+    assert np.abs(th - np.sort(lam)).max() <= 1e-12 * 60
+    assert np.abs(G @ Z - Z * th).max() <= 1e-12 * 60
+
+
 def test_heev_small_degenerate(cuda, orc):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(41)
