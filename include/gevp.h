@@ -182,6 +182,33 @@ gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* 
 /* Measured FP64 FMA, FP64 DMMA and FP32 FMA rates of this device in TFLOP/s (host out[3]). */
 gevp_status gevp_probe_peaks(gevp_handle h, double* out);
 
+/* ---- allocation-free variant ------------------------------------------------------- */
+
+/* Size, in complex128 elements, of the fixed device scratch of the entry point below
+ * (32 MiB on every device that loads the library, held until the process exits). */
+#define GEVP_NOALLOC_MAX_ELEMS (1 << 21)
+
+/* The FP64 Chebyshev filter of gevp_chebyshev_filter (prec GEVP_PREC_FP64), for callers
+ * that must not allocate device memory when they call it: code running while a CUDA
+ * graph is being captured (where a cudaMalloc is illegal or would be recorded into the
+ * graph), applications whose device memory belongs to a pool allocator such as
+ * PyTorch's caching allocator (a library cudaMalloc/cudaFree would bypass the pool and
+ * synchronise the device), and services that reserve a fixed memory budget at start-up.
+ * The paper has no counterpart; it is a deployment variant of the same computation.
+ *   No handle: the work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *   stream) of the current device and the call returns without waiting for it. C, Y as in
+ *   gevp_chebyshev_filter (device, row-major complex128, Y n x m overwritten in place).
+ *   It calls no cudaMalloc, cudaFree or allocating library routine. Its scratch, two n x m
+ *   blocks, is a fixed array in the library's device image: requires 2 n m <=
+ *   GEVP_NOALLOC_MAX_ELEMS, else GEVP_ERR_INVALID_ARG is returned and nothing is enqueued.
+ *   The first call on a device looks up the array's device address (once per device, with
+ *   that device current); make that first call before any stream capture. Every call on a
+ *   device shares the one array, which keeps the previous call's contents (each call
+ *   writes every scratch element it reads first, so nothing needs clearing): calls whose
+ *   work overlaps on the GPU (other streams, other host threads) race on it. */
+gevp_status gevp_chebyshev_filter_noalloc(void* stream, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy,
+                                          int m, int degree, double lo, double hi, double s);
+
 /* Number of kernels the handle launched since creation (for launch accounting). */
 int64_t gevp_kernel_launches(gevp_handle h);
 
