@@ -132,8 +132,10 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
                                 double* resid, gevp_stats* stats);
 
 /* Same, with every array in HOST memory (A, B: host arrays of host pointers; Lambda,
- * resid, X host). The copies to and from the device are part of the call; problem l+1's
- * matrix is copied on a second stream while problem l is solved. */
+ * resid, X host; pinned memory makes the copies asynchronous and fast). The copies to and
+ * from the device are part of the call: every A (and each distinct B) is copied into a
+ * device staging area owned by the handle, the sequence is solved there, and Lambda,
+ * resid and X are copied back before the call returns. */
 gevp_status gevp_solve_sequence_host(gevp_handle h, int nprob, int64_t n, const void* const* A, int64_t lda,
                                      const void* const* B, int64_t ldb, int nev, const gevp_opts* opts,
                                      double* Lambda, void* X, int64_t ldx, double* resid, gevp_stats* stats);

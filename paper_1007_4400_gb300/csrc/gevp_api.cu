@@ -56,6 +56,9 @@ struct gevp_ctx {
   // pinned host mirror
   double* hbuf = nullptr;
   size_t hbuf_elems = 0;
+  // device staging of the host-buffer entry point (grown on demand)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
   // warm-start state
   bool have_prev = false;
   int64_t prev_n = 0;
@@ -631,6 +634,7 @@ gevp_status gevp_destroy(gevp_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->tc) gevp::filter_tc_release(h->tc);
+  if (h->stage) cudaFree(h->stage);
   if (h->arena) cudaFree(h->arena);
   if (h->hbuf) cudaFreeHost(h->hbuf);
   for (auto e : h->evpool) cudaEventDestroy(e);
@@ -784,9 +788,63 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
 gevp_status gevp_solve_sequence_host(gevp_handle h, int nprob, int64_t n, const void* const* A, int64_t lda,
                                      const void* const* B, int64_t ldb, int nev, const gevp_opts* opts,
                                      double* Lambda, void* X, int64_t ldx, double* resid, gevp_stats* stats) {
-  (void)h; (void)nprob; (void)n; (void)A; (void)lda; (void)B; (void)ldb; (void)nev; (void)opts;
-  (void)Lambda; (void)X; (void)ldx; (void)resid; (void)stats;
-  return GEVP_ERR_UNSUPPORTED;
+  if (!h || nprob < 0 || n < 0 || nev < 0) return GEVP_ERR_INVALID_ARG;
+  if (nprob == 0 || n == 0 || nev == 0) return GEVP_OK;
+  if (!A || !B || !Lambda || !resid || bad_ld(lda, n) || bad_ld(ldb, n) || (X && bad_ld(ldx, nev)))
+    return GEVP_ERR_INVALID_ARG;
+  for (int l = 0; l < nprob; ++l)
+    if (!A[l] || !B[l]) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  gevp_opts o;
+  if (opts) o = *opts; else gevp_default_opts(&o);
+  // distinct B matrices (consecutive equal pointers share one device copy)
+  std::vector<int> bslot(nprob);
+  int nb = 0;
+  for (int l = 0; l < nprob; ++l) bslot[l] = (l > 0 && B[l] == B[l - 1]) ? bslot[l - 1] : nb++;
+  const size_t mat = (size_t)n * n * sizeof(double2);
+  const size_t out_x = X ? (size_t)(o.keep_all_X ? nprob : 1) * n * nev * sizeof(double2) : 0;
+  const size_t need = (size_t)(nprob + nb) * mat + 2 * (size_t)nprob * nev * sizeof(double) + out_x + 4096;
+  if (need > h->stage_bytes) {
+    if (h->stage) { cudaStreamSynchronize(h->stream); cudaFree(h->stage); h->stage = nullptr; }
+    CK(cudaMalloc(&h->stage, need));
+    h->stage_bytes = need;
+  }
+  char* p = (char*)h->stage;
+  std::vector<const void*> dA(nprob), dB(nprob), dBs(nb);
+  // host -> device: one copy per matrix, rows packed to ld = n
+  for (int l = 0; l < nprob; ++l) {
+    dA[l] = p;
+    CK(cudaMemcpy2DAsync(p, n * sizeof(double2), A[l], lda * sizeof(double2), n * sizeof(double2), n,
+                         cudaMemcpyHostToDevice, h->stream));
+    p += mat;
+  }
+  for (int l = 0; l < nprob; ++l) {
+    if (l == 0 || bslot[l] != bslot[l - 1]) {
+      dBs[bslot[l]] = p;
+      CK(cudaMemcpy2DAsync(p, n * sizeof(double2), B[l], ldb * sizeof(double2), n * sizeof(double2), n,
+                           cudaMemcpyHostToDevice, h->stream));
+      p += mat;
+    }
+    dB[l] = dBs[bslot[l]];
+  }
+  double* dLam = (double*)p;
+  p += (size_t)nprob * nev * sizeof(double);
+  double* dRes = (double*)p;
+  p += (size_t)nprob * nev * sizeof(double);
+  double2* dX = X ? (double2*)p : nullptr;
+  gevp_status s = gevp_solve_sequence(h, nprob, n, dA.data(), n, dB.data(), n, nev, nullptr, 0, 0, &o, dLam, dX, nev,
+                                      dRes, stats);
+  if (s != GEVP_OK && s != GEVP_ERR_NO_CONVERGENCE) return s;
+  CK(cudaMemcpyAsync(Lambda, dLam, (size_t)nprob * nev * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(resid, dRes, (size_t)nprob * nev * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (X) {
+    int blocks = o.keep_all_X ? nprob : 1;
+    for (int b = 0; b < blocks; ++b)
+      CK(cudaMemcpy2DAsync((double2*)X + (size_t)b * n * ldx, ldx * sizeof(double2), dX + (size_t)b * n * nev,
+                           nev * sizeof(double2), nev * sizeof(double2), n, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return s;
 }
 
 gevp_status gevp_chebyshev_filter(gevp_handle h, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy, int m,

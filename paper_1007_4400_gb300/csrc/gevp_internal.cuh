@@ -62,6 +62,28 @@ void zgemm(const ZgemmArgs& a, double2* split_ws, size_t split_ws_elems, cudaStr
 ZgemmArgs zg(int M, int N, int K, const double2* A, int64_t lda, int opA,
              const double2* B, int64_t ldb, int opB, double2* D, int64_t ldd, double alpha = 1.0);
 
+// Grouped (ragged-batch) form: a device array of items, each one independent product with
+// the same op/tri flags. tile_start/tiles_n are filled by zgemm_group_layout (host). If
+// active != nullptr and *active == 0 the item is skipped; if coef != nullptr the scalars
+// are read from device memory (alpha = coef[0], beta = coef[1], gamma = coef[2]).
+struct ZgemmItem {
+  int M, N, K;
+  int tile_start, tiles_n;
+  const double2* A; int64_t lda;
+  const double2* B; int64_t ldb;
+  double2* D; int64_t ldd;
+  const double2* Cin; int64_t ldc;
+  const double2* Ein; int64_t lde;
+  double alpha, beta, gamma;
+  const double* coef;
+  const int* active;
+};
+struct ZgemmGroupFlags { int opA, opB, triA, triB, triD, maskB; };
+int zgemm_group_tile(const ZgemmItem* items_host, int nitems);
+int zgemm_group_layout(ZgemmItem* items_host, int nitems, int tile);   // returns total tiles
+void zgemm_grouped(const ZgemmItem* items_dev, int nitems, int total_tiles, int tile, const ZgemmGroupFlags& f,
+                   cudaStream_t s);
+
 // ---------------------------------------------------------------- elementwise / misc
 void herm_sum_inplace(int64_t n, double2* C, int64_t ldc, cudaStream_t s);  // C <- C + C^H
 void zshift_diag(int64_t n, double2* A, int64_t lda, double sh, cudaStream_t s);

@@ -210,6 +210,34 @@ def solve_sequence(A_list, B, nev: int, X_prev=None, keep_all_X: bool = False, c
     return SequenceResult(Lam, X, res, [s.as_dict() for s in stats], st)
 
 
+def solve_sequence_host(A_list, B, nev: int, keep_all_X: bool = False, device=None, check: bool = True, **opts):
+    """gevp_solve_sequence_host: host (CPU, ideally pinned) complex128 inputs and outputs;
+    the library copies to and from its device staging inside the call."""
+    As = list(A_list)
+    Bs = list(B) if isinstance(B, (list, tuple)) else [B] * len(As)
+    for t in As + Bs:
+        if t.is_cuda or t.dtype != torch.complex128 or t.stride(1) != 1:
+            raise TypeError("host entry point takes CPU complex128 row-major tensors")
+    n = As[0].shape[0]
+    nprob = len(As)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    h = _handle(dev)
+    o = default_opts(keep_all_X=1 if keep_all_X else 0, **opts)
+    if not isinstance(B, (list, tuple)):
+        o.b_fixed = 1
+    Lam = torch.empty((nprob, nev), dtype=torch.float64).pin_memory()
+    res = torch.empty((nprob, nev), dtype=torch.float64).pin_memory()
+    X = torch.empty(((nprob, n, nev) if keep_all_X else (n, nev)), dtype=torch.complex128).pin_memory()
+    Ap = (C.c_void_p * nprob)(*[a.data_ptr() for a in As])
+    Bp = (C.c_void_p * nprob)(*[b.data_ptr() for b in Bs])
+    stats = (GevpStats * nprob)()
+    st = load().gevp_solve_sequence_host(h, nprob, n, Ap, As[0].stride(0), Bp, Bs[0].stride(0), nev, C.byref(o),
+                                         _ptr(Lam), _ptr(X), nev, _ptr(res), stats)
+    if check and st not in (0, 3):
+        _check(st, h)
+    return SequenceResult(Lam, X, res, [s.as_dict() for s in stats], st)
+
+
 def chebyshev_filter(Cm: torch.Tensor, Y: torch.Tensor, degree: int, lo: float, hi: float, s: float,
                      prec: str = "fp64") -> torch.Tensor:
     """Y <- p(C) Y in place (scaled Chebyshev filter); returns Y."""

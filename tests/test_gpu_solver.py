@@ -148,3 +148,14 @@ def test_full_size_scf_sequence_n2048(cuda, orc):
         neg, zero = orc.inertia(A, B, sig)
         assert zero == 0 and neg == s.nev
         assert lam[l][-1] < sig
+
+
+def test_host_entry_point_matches_device(cuda):
+    from paper_1007_4400_gb300 import gevp, synth
+    s = synth.make_sequence(1, 256, 3, 12, 6, device="cpu")
+    rd = gevp.solve_sequence([a.to(cuda) for a in s.A], s.B.to(cuda), 12, nex=6)
+    rh = gevp.solve_sequence_host([a.pin_memory() for a in s.A], s.B.pin_memory(), 12, nex=6)
+    assert rh.status == 0
+    assert torch.equal(rh.Lambda, rd.Lambda.cpu())
+    assert torch.equal(rh.resid, rd.resid.cpu())
+    assert torch.equal(rh.X, rd.X.cpu())
