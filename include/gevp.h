@@ -140,6 +140,61 @@ gevp_status gevp_solve_sequence_host(gevp_handle h, int nprob, int64_t n, const 
                                      const void* const* B, int64_t ldb, int nev, const gevp_opts* opts,
                                      double* Lambda, void* X, int64_t ldx, double* resid, gevp_stats* stats);
 
+/* ---- batched (k-point) form --------------------------------------------------------- */
+
+/* Counters of one gevp_solve_batched call. Times are CUDA-event milliseconds summed over
+ * the steps of the sequence. */
+typedef struct {
+  int steps;            /* problems per k-point (the sequence length)                   */
+  int rounds;           /* lock-step rounds (filter + CholQR + Rayleigh-Ritz), all steps */
+  int max_rounds_step;  /* most rounds any one step needed                              */
+  int graph_replays;    /* rounds executed as replays of the captured round graph      */
+  int switches;         /* problems switched to the FP64 filter (all steps)            */
+  int orth_fallbacks;   /* CholQR breakdowns repaired by a random restart              */
+  int final_passes;     /* original-space checks, summed over problems and steps        */
+  int converged;        /* 1 if every residual of every problem <= tol                 */
+  int tile[8];          /* autotuner: grouped FP64 GEMM tile chosen per call class      */
+  int deg_cap[8];       /* autotuner: filter degree cap per size bucket (last step)     */
+  double max_resid;
+  double flops_fp64, flops_lowp;   /* executed-flop model                              */
+  float ms_chol, ms_reduce, ms_bounds, ms_rounds, ms_final, ms_total;
+} gevp_batch_stats;
+
+/* Many independent problem sequences of uneven size at once: the paper solves Eq. 3 for
+ * every k-point of the Brillouin-zone sampling and every self-consistent iteration (the
+ * paragraph after Eq. 3). nk k-points, each a sequence of nsteps problems
+ * A_{k,l} x = lambda B_k x of order n[k] with B_k fixed along the sequence; each step l
+ * is warm-started from step l-1's eigenvectors of the same k-point. All k-points advance
+ * in lock-step rounds: every phase of a round is one launch for the whole batch (grouped
+ * GEMMs over a global tile list, one CTA per problem for the small dense work, one
+ * grouped tcgen05 launch per filter step), converged k-points are skipped by device
+ * flags, and a round is captured once as a CUDA graph and replayed. An autotuner picks
+ * the grouped GEMM tile per call class (timed on the first round of a new batch shape)
+ * and the filter degree cap per size bucket (a cost model fed by measured times and the
+ * Chebyshev convergence factors of the previous step).
+ *   n, nev, nex: host arrays of nk (nex nullable: opts->nex for all, at least 2 used);
+ *   m_k = min(n_k, nev_k + nex_k) <= 1024.
+ *   A: host array of nk * nsteps device pointers, A[k * nsteps + l] (ld lda[k]);
+ *   B: host array of nk device pointers (ld ldb[k]), HPD.
+ *   X_prev: nullable host array of nk (entries nullable) device pointers, n_k x kprev[k]
+ *   (ld ldxp[k]) start vectors for step 0 in the original space.
+ *   Lambda, resid: host arrays of nk device pointers, each nsteps x nev_k.
+ *   X: nullable host array of nk device pointers, n_k x nev_k (ld ldx[k]) eigenvectors of
+ *   the last step (or nsteps such blocks, stride n_k * ldx[k], if opts->keep_all_X).
+ *   opts: filter_prec FP64, FP32 or BF16 (low precision switches a k-point to FP64 when
+ *   it stalls); tol, max_outer (rounds per step), deg_min, deg_max (<= 64), seed,
+ *   cold_start, lanczos_steps, refine_iters as for gevp_solve_sequence; b_fixed is implied.
+ *   stats: nullable.
+ *   The handle keeps the batch's workspace, autotuner choices and round graph for the
+ *   next call with the same shapes; a call with other shapes rebuilds them.
+ *   Returns GEVP_ERR_NOT_HPD if some B_k is not HPD, GEVP_ERR_NO_CONVERGENCE if some
+ *   residual stays above tol (all outputs written). */
+gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, const int64_t* n, const int* nev, const int* nex,
+                               const void* const* A, const int64_t* lda, const void* const* B, const int64_t* ldb,
+                               const void* const* X_prev, const int64_t* ldxp, const int* kprev,
+                               const gevp_opts* opts, double* const* Lambda, double* const* resid,
+                               void* const* X, const int64_t* ldx, gevp_batch_stats* stats);
+
 /* ---- individual steps of the solver (same kernels as the solver uses) ---------------- */
 
 /* Scaled Chebyshev filter (Zhou, Saad, Tiago & Chelikowsky 2006), in place:

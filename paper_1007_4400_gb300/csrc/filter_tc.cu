@@ -130,15 +130,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__global__ void __launch_bounds__(128, 1) cheb_tc_kernel(const __grid_constant__ TcMaps maps, TcParams p) {
+// One output tile: rows m0..m0+127 of C times columns c0..c0+nchunk-1 of the block over
+// K slice z. amaps/bmaps: the tensor maps of the pieces of C and of the block (kernel
+// parameter space or global memory).
+__device__ __forceinline__ void tc_tile(const CUtensorMap* amaps, const CUtensorMap* bmaps, const TcParams& p,
+                                        int m0, int c0, int z) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_sh;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.x * TM;
-  const int c0 = blockIdx.y * p.nchunk;
-  const int z = blockIdx.z;
   const int nkb_total = p.n_pad / TK;
   const int kb0 = z * p.kb_per_split;
   const int kb1 = min(kb0 + p.kb_per_split, nkb_total);
@@ -178,8 +179,8 @@ __global__ void __launch_bounds__(128, 1) cheb_tc_kernel(const __grid_constant__
       mbar_expect_tx(&full[s], stage_bytes);
       const int seg = i / nkb;
       const int kx = (kb0 + i % nkb) * TK;
-      const CUtensorMap* A = &maps.a[3 * kSegA[seg]];
-      const CUtensorMap* B = &maps.b[3 * kSegB[seg]];
+      const CUtensorMap* A = amaps + 3 * kSegA[seg];
+      const CUtensorMap* B = bmaps + 3 * kSegB[seg];
       tma_load_2d(tile(s, 0), A + 0, kx, m0, &full[s]);
       tma_load_2d(tile(s, 1), A + 1, kx, m0, &full[s]);
       tma_load_2d(tile(s, 2), A + 2, kx, m0, &full[s]);
@@ -239,6 +240,10 @@ __global__ void __launch_bounds__(128, 1) cheb_tc_kernel(const __grid_constant__
   }
 }
 
+__global__ void __launch_bounds__(128, 1) cheb_tc_kernel(const __grid_constant__ TcMaps maps, TcParams p) {
+  tc_tile(maps.a, maps.b, p, blockIdx.x * TM, blockIdx.y * p.nchunk, blockIdx.z);
+}
+
 // Split v into nsplit BF16 pieces written at stride `ps` (piece p at base + p * ps).
 __device__ __forceinline__ void split_store(double v, int nsplit, __nv_bfloat16* base, size_t ps, int64_t e) {
   double r = v;
@@ -265,9 +270,10 @@ struct YPlanes {
 // ksplit = 0 means the product term is zero (first step of the corrected filter).
 // With R non-null the forcing term pc[col] * R[col][row] is added (residual-corrected
 // filter: the recurrence runs on the defect D_j = p_j(C) Q - Q p_j(Theta)).
-__global__ void cheb_tc_epilogue(int n, int ncols, int n_pad, int ncols_pad, int ksplit, const float2* ws,
-                                 const float2* cur, const float2* prev, float2* outp, YPlanes yp, float alpha,
-                                 float beta, float gamma, const float2* R, const float* pc) {
+__device__ __forceinline__ void tc_epilogue_body(int n, int ncols, int n_pad, int ncols_pad, int ksplit,
+                                                 const float2* ws, const float2* cur, const float2* prev, float2* outp,
+                                                 const YPlanes& yp, float alpha, float beta, float gamma,
+                                                 const float2* R, const float* pc) {
   int64_t total = (int64_t)ncols_pad * n_pad;
   int64_t plane = total;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -304,11 +310,17 @@ __global__ void cheb_tc_epilogue(int n, int ncols, int n_pad, int ncols_pad, int
   }
 }
 
+__global__ void cheb_tc_epilogue(int n, int ncols, int n_pad, int ncols_pad, int ksplit, const float2* ws,
+                                 const float2* cur, const float2* prev, float2* outp, YPlanes yp, float alpha,
+                                 float beta, float gamma, const float2* R, const float* pc) {
+  tc_epilogue_body(n, ncols, n_pad, ncols_pad, ksplit, ws, cur, prev, outp, yp, alpha, beta, gamma, R, pc);
+}
+
 // R^T = (W - Q diag(theta))^T in FP32 (residual of the Rayleigh-Ritz pairs), transposed.
-__global__ void resid_to_state(int n, int m, int n_pad, int ncols_pad, const double2* Q, int64_t ldq,
-                               const double2* W, int64_t ldw, const double* theta, float2* Rt) {
+__device__ __forceinline__ void resid_to_state_body(int n, int m, int n_pad, int ncols_pad, const double2* Q,
+                                                    int64_t ldq, const double2* W, int64_t ldw, const double* theta,
+                                                    float2* Rt, int r0, int c0) {
   __shared__ float2 t[32][33];
-  int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int k = ty; k < 32; k += 8) {
     int r = r0 + k, c = c0 + tx;
@@ -327,11 +339,16 @@ __global__ void resid_to_state(int n, int m, int n_pad, int ncols_pad, const dou
   }
 }
 
+__global__ void resid_to_state(int n, int m, int n_pad, int ncols_pad, const double2* Q, int64_t ldq,
+                               const double2* W, int64_t ldw, const double* theta, float2* Rt) {
+  resid_to_state_body(n, m, n_pad, ncols_pad, Q, ldq, W, ldw, theta, Rt, blockIdx.x * 32, blockIdx.y * 32);
+}
+
 // Y = Q diag(pd) + D (FP64 out, row-major): the filtered block from the defect D^T.
-__global__ void defect_to_y(int n, int m, int n_pad, const float2* Dt, const double2* Q, int64_t ldq,
-                            const double* pd, double2* Y, int64_t ldy) {
+__device__ __forceinline__ void defect_to_y_body(int n, int m, int n_pad, const float2* Dt, const double2* Q,
+                                                 int64_t ldq, const double* pd, double2* Y, int64_t ldy, int r0,
+                                                 int c0) {
   __shared__ float2 t[32][33];
-  int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int k = ty; k < 32; k += 8) {
     int c = c0 + k, r = r0 + tx;
@@ -347,6 +364,11 @@ __global__ void defect_to_y(int n, int m, int n_pad, const float2* Dt, const dou
       Y[(int64_t)r * ldy + c] = make_double2(fma(q.x, p, (double)d.x), fma(q.y, p, (double)d.y));
     }
   }
+}
+
+__global__ void defect_to_y(int n, int m, int n_pad, const float2* Dt, const double2* Q, int64_t ldq,
+                            const double* pd, double2* Y, int64_t ldy) {
+  defect_to_y_body(n, m, n_pad, Dt, Q, ldq, pd, Y, ldy, blockIdx.x * 32, blockIdx.y * 32);
 }
 
 // C (FP64, n x n) -> BF16 pieces [piece][re, im, re+im][n_pad][n_pad] (zero padding).
@@ -675,6 +697,153 @@ cudaError_t filter_tc_apply_corrected(FilterTC* f, int64_t n, int m, const doubl
 cudaError_t filter_tc_product(FilterTC* f, int64_t n, int m, const double2* Y, int64_t ldy, double2* D, int64_t ldd,
                               int nsplit, int* err_host, cudaStream_t s) {
   return run_filter(f, n, m, Y, ldy, nullptr, 0, nullptr, nullptr, D, ldd, 1, -1.0, 1.0, 1.0, nsplit, err_host, s);
+}
+
+// ===================================================================== grouped form
+// The residual-corrected filter for every problem of a k-point batch at once: one launch
+// per recurrence step covers the output tiles of all problems (a global tile list with a
+// prefix sum per problem, BDesc::unit_start), and one launch per step applies the
+// recurrence to all problems. The coefficients, the degree and the activity of each
+// problem are read from device memory (BDesc::fco, pcoef, pfinal, flags), so the launch
+// sequence is the same in every round and is captured once. The tensor maps live in
+// global memory, 18 per problem.
+namespace {
+
+__device__ __forceinline__ bool tcg_runs(const BDesc& d, int j) { return d.flags[6] != 0 && j < d.flags[1]; }
+
+__global__ void __launch_bounds__(128, 1) cheb_tcg_kernel(const BDesc* D, int np, int j, int* err) {
+  const int u = blockIdx.x;
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (D[mid].unit_start <= u) lo = mid; else hi = mid - 1;
+  }
+  const BDesc& d = D[lo];
+  if (!tcg_runs(d, j)) return;
+  const int local = u - d.unit_start;
+  const int per_z = d.mtiles * d.nchunks;
+  const int z = local / per_z, r = local % per_z;
+  if (z >= d.ks) return;
+  TcParams p;
+  p.n_pad = d.n_pad;
+  p.nchunk = d.nchunk;
+  p.kb_per_split = d.kbps;
+  p.ncols_pad = d.ncols_pad;
+  p.nseg = d.nseg;
+  p.tmem_cols = d.tmem_cols;
+  p.ws = d.tws;
+  p.err = err;
+  const CUtensorMap* maps = (const CUtensorMap*)d.maps;
+  tc_tile(maps, maps + MAXSPLIT * 3, p, (r / d.nchunks) * TM, (r % d.nchunks) * d.nchunk, z);
+}
+
+// j = 0: D_1 = alpha_0 R; j >= 1: D_{j+1} from the split-K partials of C D_j. D_k is kept
+// in S[(k - 1) mod 3].
+__global__ void tcg_epilogue(const BDesc* D, int j) {
+  const BDesc& d = D[blockIdx.y];
+  if (!tcg_runs(d, j)) return;
+  float2* S[3] = {d.S0, d.S1, d.S2};
+  float2* outp = S[j % 3];
+  const float2* cur = j >= 1 ? S[(j - 1) % 3] : nullptr;
+  const float2* prev = j >= 2 ? S[(j - 2) % 3] : nullptr;
+  const float al = j >= 1 ? (float)d.fco[3 * j] : 0.f;
+  const float be = j >= 1 ? (float)d.fco[3 * j + 1] : 0.f;
+  const float ga = j >= 1 ? (float)d.fco[3 * j + 2] : 0.f;
+  YPlanes yp{d.Yp, (size_t)d.ncols_pad * d.n_pad, d.nsplit};
+  tc_epilogue_body(d.n, d.m, d.n_pad, d.ncols_pad, j >= 1 ? d.ks : 0, d.tws, cur, prev, outp, yp, al, be, ga, d.S3,
+                   d.pcoef + (size_t)j * d.ncols_pad);
+}
+
+__global__ void tcg_resid_to_state(const BDesc* D) {
+  const BDesc& d = D[blockIdx.z];
+  if (d.flags[6] == 0) return;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  if (r0 >= d.n_pad || c0 >= d.ncols_pad) return;
+  resid_to_state_body(d.n, d.m, d.n_pad, d.ncols_pad, d.Q, d.m, d.W, d.m, d.theta, d.S3, r0, c0);
+}
+
+// Y1 = Q diag(p_deg(theta)) + D_deg
+__global__ void tcg_defect_to_y(const BDesc* D) {
+  const BDesc& d = D[blockIdx.z];
+  if (d.flags[6] == 0) return;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  if (r0 >= d.n || c0 >= d.m) return;
+  float2* S[3] = {d.S0, d.S1, d.S2};
+  const int deg = d.flags[1];
+  defect_to_y_body(d.n, d.m, d.n_pad, S[(deg - 1) % 3], d.Q, d.m, d.pfinal, d.Y1, d.m, r0, c0);
+}
+
+__global__ void tcg_c_to_planes(const BDesc* D) {
+  const BDesc& d = D[blockIdx.y];
+  if (d.flags[0] == 0) return;
+  const int64_t n = d.n, n_pad = d.n_pad, total = n_pad * n_pad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / n_pad, k = e % n_pad;
+    double2 v = (i < n && k < n) ? d.C[i * n + k] : make_double2(0.0, 0.0);
+    split_store(v.x, d.nsplit, d.Cp, 3 * (size_t)total, e);
+    split_store(v.y, d.nsplit, d.Cp + total, 3 * (size_t)total, e);
+    split_store(v.x + v.y, d.nsplit, d.Cp + 2 * total, 3 * (size_t)total, e);
+  }
+}
+
+}  // namespace
+
+void tcg_geometry(int64_t n, int m, int* n_pad, int* ncols_pad, int* nchunk, int* nchunks) {
+  *n_pad = pad_to((int)n, TM);
+  chunking(m, nchunks, nchunk);
+  *ncols_pad = *nchunks * *nchunk;
+}
+
+int tcg_nseg(int nsplit) { return nseg_for(nsplit); }
+
+size_t tcg_smem_bytes(int nchunk_max) {
+  return (size_t)STAGES * (3 * TM * TK * 2 + 3 * (size_t)nchunk_max * TK * 2) + 1024;
+}
+
+size_t tcg_map_bytes() { return sizeof(CUtensorMap) * MAXSPLIT * 3 * 2; }
+
+bool tcg_encode_maps(const BDesc& d, void* maps_host) {
+  CUtensorMap* a = (CUtensorMap*)maps_host;
+  CUtensorMap* b = a + MAXSPLIT * 3;
+  std::memset(maps_host, 0, tcg_map_bytes());
+  const size_t cplane = (size_t)d.n_pad * d.n_pad, yplane = (size_t)d.ncols_pad * d.n_pad;
+  for (int pc = 0; pc < d.nsplit; ++pc)
+    for (int part = 0; part < 3; ++part) {
+      if (!encode_2d(&a[3 * pc + part], d.Cp + (3 * pc + part) * cplane, d.n_pad, d.n_pad, TK, TM) ||
+          !encode_2d(&b[3 * pc + part], d.Yp + (3 * pc + part) * yplane, d.n_pad, d.ncols_pad, TK, d.nchunk))
+        return false;
+    }
+  return true;
+}
+
+void tcg_set_matrix(const BDesc* D, int np, int64_t npad2_max, cudaStream_t s) {
+  int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((npad2_max + 255) / 256, 256));
+  tcg_c_to_planes<<<dim3(blocks, np), 256, 0, s>>>(D);
+  LAUNCH_NOTE(1);
+}
+
+cudaError_t tcg_prepare(int nchunk_max) {
+  return cudaFuncSetAttribute(cheb_tcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tcg_smem_bytes(nchunk_max));
+}
+
+// The launch sequence of one filter application (no host synchronisation, capturable);
+// tcg_prepare must have been called for this nchunk_max first.
+cudaError_t tcg_filter(const BDesc* D, const TcgShape& g, int* err, cudaStream_t s) {
+  const size_t smem = tcg_smem_bytes(g.nchunk_max);
+  dim3 tg((g.n_pad_max + 31) / 32, (g.ncols_pad_max + 31) / 32, g.np);
+  int eb = (int)std::max<int64_t>(1, std::min<int64_t>((g.nc_max + 255) / 256, 64));
+  tcg_resid_to_state<<<tg, 256, 0, s>>>(D);
+  tcg_epilogue<<<dim3(eb, g.np), 256, 0, s>>>(D, 0);
+  LAUNCH_NOTE(2);
+  for (int j = 1; j < g.steps; ++j) {
+    cheb_tcg_kernel<<<g.units, 128, smem, s>>>(D, g.np, j, err);
+    tcg_epilogue<<<dim3(eb, g.np), 256, 0, s>>>(D, j);
+    LAUNCH_NOTE(2);
+  }
+  tcg_defect_to_y<<<tg, 256, 0, s>>>(D);
+  LAUNCH_NOTE(1);
+  return cudaGetLastError();
 }
 
 }  // namespace gevp

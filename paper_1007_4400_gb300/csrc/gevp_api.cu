@@ -69,7 +69,15 @@ struct gevp_ctx {
   std::vector<cudaEvent_t> evpool;
   std::string err;
   gevp::FilterTC* tc = nullptr;
+  gevp::BatchPlan* batch = nullptr;   // state of the batched (k-point) entry point
 };
+
+namespace gevp {
+cudaStream_t ctx_stream(gevp_ctx* h) { return h->stream; }
+int ctx_device(gevp_ctx* h) { return h->device; }
+void ctx_set_error(gevp_ctx* h, const char* msg) { h->err = msg; }
+BatchPlan*& ctx_batch(gevp_ctx* h) { return h->batch; }
+}  // namespace gevp
 
 namespace {
 
@@ -634,6 +642,7 @@ gevp_status gevp_destroy(gevp_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->tc) gevp::filter_tc_release(h->tc);
+  if (h->batch) gevp::batch_release(h->batch);
   if (h->stage) cudaFree(h->stage);
   if (h->arena) cudaFree(h->arena);
   if (h->hbuf) cudaFreeHost(h->hbuf);

@@ -170,6 +170,99 @@ cudaError_t filter_tc_apply_corrected(FilterTC* f, int64_t n, int m, const doubl
 cudaError_t filter_tc_product(FilterTC* f, int64_t n, int m, const double2* Y, int64_t ldy, double2* D, int64_t ldd,
                               int nsplit, int* err_host, cudaStream_t s);
 
+// ---------------------------------------------------------------- batched (k-point) form
+// One descriptor per problem of a batch, in device memory; batched kernels take the array
+// and select their problem by a block index. Problems whose *active flag is zero return
+// at once, so a launch sequence keeps its shape while problems converge. Every n x m
+// block has ld = m, every m x m block ld = m, every n x n matrix ld = n.
+constexpr int kBDegMax = 64;   // highest filter degree of the batched form
+struct BDesc {
+  int n, m, nev, kl;          // kl: Lanczos steps
+  const double2* A; int64_t lda;
+  const double2* B; int64_t ldb;
+  double2 *L, *Linv, *C, *T;  // n x n
+  float2* M32;                // n x n FP32 copy for Lanczos
+  double2 *Q, *Y1, *Y2, *W, *Wt, *Xf;   // n x m
+  double2 *G, *Zs, *Gw, *Gwi;           // m x m
+  // small eigensolver
+  float2 *G32, *Z32; float* w32; int* perm;
+  double2 *hZ, *hR, *hS, *hT, *hE;      // m x m
+  double *hlam, *hscal;
+  // Lanczos
+  float2 *V, *lvec, *T32, *LZ32; float *ab, *lw32; int* lperm;
+  // per-column and per-problem scalars
+  double *theta, *res, *lamf, *resf, *dscale, *partial;
+  double* bounds;             // see bkernels.cu for the slot map
+  double* fco;                // [kBDegMax][3] recurrence coefficients of the current round
+  int* flags;                 // [0] active, [1] degree, [2] info, [3] state, [4] rounds,
+                              // [5] fp64 filter, [6] filter active (tc), [7] filter active (fp64)
+  int* stepact;               // [kBDegMax] FP64 filter: step j runs for this problem
+  const int* active;          // = flags
+  // tensor-core filter state
+  int n_pad, ncols_pad, nchunk, nchunks, mtiles, ks, kbps, nseg;
+  unsigned tmem_cols; int unit_start;
+  const void* maps;           // 18 CUtensorMap (C pieces, then block pieces), 64-byte aligned
+  __nv_bfloat16 *Cp, *Yp;
+  float2 *S0, *S1, *S2, *S3, *tws;
+  float* pcoef;               // [kBDegMax][ncols_pad]
+  double* pfinal;             // [ncols_pad]
+  int nsplit, pad_;
+};
+
+void bk_herm_sum(const BDesc* D, int np, int64_t nmax, cudaStream_t s);
+void bk_to_c32(const BDesc* D, int np, int64_t nmax, int which, cudaStream_t s);
+void bk_hermitize_lower_G(const BDesc* D, int np, int mmax, cudaStream_t s);
+void bk_gram_scale(const BDesc* D, int np, double shift_factor, cudaStream_t s);
+void bk_col_scale(const BDesc* D, int np, int64_t nm_max, int which, cudaStream_t s);
+void bk_copy_nm(const BDesc* D, int np, int64_t nm_max, int from, int to, cudaStream_t s);
+void bk_potrf_small(const BDesc* D, int np, cudaStream_t s);
+void bk_trtri_small(const BDesc* D, int np, cudaStream_t s);
+void bk_step_reset(const BDesc* D, int np, double tol, int filter64, cudaStream_t s);
+void bk_lanczos(const BDesc* D, int np, int64_t nmax, int k, int use_count, int out_off, uint64_t seed,
+                cudaStream_t s);
+void bk_post_bounds(const BDesc* D, int np, cudaStream_t s);
+void bk_heev_prep(const BDesc* D, int np, int mmax, cudaStream_t s);
+void bk_oa_scalars(const BDesc* D, int np, cudaStream_t s);
+void bk_oa_update(const BDesc* D, int np, int mmax, int only_orth, cudaStream_t s);
+void bk_hermitize_avg_S(const BDesc* D, int np, int mmax, cudaStream_t s);
+void bk_sort_pairs(const BDesc* D, int np, int zsel, cudaStream_t s);
+void bk_resid(const BDesc* D, int np, int mmax, cudaStream_t s);
+void bk_final_check(const BDesc* D, int np, int nevmax, cudaStream_t s);
+void bk_final_status(const BDesc* D, int np, int* out, cudaStream_t s);
+void bk_cheb_coef(const BDesc* D, int np, int deg_min, const int* deg_cap, cudaStream_t s);
+void bk_fp64_select(const BDesc* D, int np, int64_t nm_max, cudaStream_t s);
+void bk_round_status(const BDesc* D, int np, int* out, cudaStream_t s);
+void bk_randn(const BDesc* D, int np, int64_t nm_max, uint64_t seed, const int* mask, cudaStream_t s);
+void bk_force_final(const BDesc* D, int np, cudaStream_t s);
+struct BOut { double* lam; double* res; double2* X; int64_t ldx; };
+void bk_write_out(const BDesc* D, const BOut* O, int np, int64_t nm_max, cudaStream_t s);
+size_t bk_partial_elems(int m);
+// batched FP32 Jacobi: which = 0 -> G32 (m x m) into Z32/w32/perm; 1 -> T32 (k x k) into LZ32/lw32/lperm
+void jacobi32_batched(const BDesc* D, int np, int which, int k, int max_sweeps, cudaStream_t s);
+void cluster_jacobi_batched(const BDesc* D, int np, int zsel, double rel, int max_sweeps, cudaStream_t s);
+
+// grouped tensor-core filter (residual-corrected recurrence) over the problems of a batch
+void tcg_geometry(int64_t n, int m, int* n_pad, int* ncols_pad, int* nchunk, int* nchunks);
+int tcg_nseg(int nsplit);
+size_t tcg_smem_bytes(int nchunk_max);
+size_t tcg_map_bytes();                                  // bytes of one problem's tensor maps
+bool tcg_encode_maps(const BDesc& d, void* maps_host);   // host copy of d's maps (Cp, Yp set)
+void tcg_set_matrix(const BDesc* D, int np, int64_t npad2_max, cudaStream_t s);
+struct TcgShape { int np, units, n_pad_max, ncols_pad_max, nchunk_max, steps; int64_t nc_max; };
+cudaError_t tcg_prepare(int nchunk_max);
+cudaError_t tcg_filter(const BDesc* D, const TcgShape& g, int* err, cudaStream_t s);
+
+// handle access for the translation units outside the main driver
+struct BatchPlan;
+void batch_release(BatchPlan* p);
+}  // namespace gevp
+struct gevp_ctx;
+namespace gevp {
+cudaStream_t ctx_stream(gevp_ctx* h);
+int ctx_device(gevp_ctx* h);
+void ctx_set_error(gevp_ctx* h, const char* msg);
+BatchPlan*& ctx_batch(gevp_ctx* h);
+
 // ---------------------------------------------------------------- probes
 void probe_peaks(double* fp64_fma_tflops, double* fp64_dmma_tflops, double* fp32_fma_tflops, cudaStream_t s);
 

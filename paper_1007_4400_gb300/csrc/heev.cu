@@ -53,8 +53,8 @@ __device__ float block_sum(float v, float* red) {
 
 // G (m x m, FP32 complex, Hermitian) is destroyed; Z receives eigenvectors (columns);
 // w receives eigenvalues sorted ascending and perm the column order (w[k] = G[perm[k]]).
-__global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* Z, float* w, int* perm,
-                                                      int max_sweeps) {
+// Executed by one CTA of JT threads.
+__device__ void jacobi32_body(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps) {
   __shared__ float4 U[512];       // per pair: (c, s, Re ph, Im ph)
   __shared__ int PQ[512][2];
   __shared__ float red[32];
@@ -157,6 +157,19 @@ __global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* 
   }
 }
 
+__global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* Z, float* w, int* perm,
+                                                      int max_sweeps) {
+  jacobi32_body(m, G, Z, w, perm, max_sweeps);
+}
+
+// one CTA per problem of a batch: which = 0 -> the Rayleigh-Ritz matrix, 1 -> Lanczos T
+__global__ void __launch_bounds__(JT) jacobi32_batched_kernel(const BDesc* D, int which, int k, int max_sweeps) {
+  const BDesc& d = D[blockIdx.x];
+  if (d.active && *d.active == 0) return;
+  if (which == 0) jacobi32_body(d.m, d.G32, d.Z32, d.w32, d.perm, max_sweeps);
+  else jacobi32_body(k, d.T32, d.LZ32, d.lw32, d.lperm, max_sweeps);
+}
+
 // Z64[:, k] = Z32[:, perm[k]]
 __global__ void gather_z_kernel(int m, const float2* Z32, const int* perm, double2* Z, int64_t ldz) {
   int64_t total = (int64_t)m * m;
@@ -247,8 +260,8 @@ __global__ void frob_kernel(int m, const double2* G, int64_t ldg, double* out) {
 // diagonal apart from those couplings. One CTA finds the pairs with |s_pq| above tol and
 // applies exact FP64 Jacobi rotations to them (S two-sided, Z on the right), a few at a
 // time, for a few sweeps; typically a handful of rotations. lam <- diag(S).
-__global__ void __launch_bounds__(1024) cluster_jacobi_kernel(int m, double2* S, double2* Z, double* lam,
-                                                              const double* fro, double rel, int max_sweeps) {
+__device__ void cluster_jacobi_body(int m, double2* S, double2* Z, double* lam, const double* fro, double rel,
+                                    int max_sweeps) {
   const double tol = rel * fro[0];
   constexpr int kMaxPairs = 256;
   __shared__ int PI[kMaxPairs], PJ[kMaxPairs];
@@ -319,6 +332,18 @@ __global__ void __launch_bounds__(1024) cluster_jacobi_kernel(int m, double2* S,
   for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = S[i * m + i].x;
 }
 
+__global__ void __launch_bounds__(1024) cluster_jacobi_kernel(int m, double2* S, double2* Z, double* lam,
+                                                              const double* fro, double rel, int max_sweeps) {
+  cluster_jacobi_body(m, S, Z, lam, fro, rel, max_sweeps);
+}
+
+__global__ void __launch_bounds__(1024) cluster_jacobi_batched_kernel(const BDesc* D, int zsel, double rel,
+                                                                      int max_sweeps) {
+  const BDesc& d = D[blockIdx.x];
+  if (d.active && *d.active == 0) return;
+  cluster_jacobi_body(d.m, d.hS, zsel == 0 ? d.hZ : d.hT, d.hlam, d.hscal + 1, rel, max_sweeps);
+}
+
 // final ordering: theta ascending, Z columns permuted accordingly
 __global__ void sort_pairs_kernel(int m, const double* lam, const double2* Zin, double* theta, double2* Z,
                                   int64_t ldz) {
@@ -350,6 +375,16 @@ size_t heev_ws_bytes(int m, size_t split_elems) {
 
 void jacobi32(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
   jacobi32_kernel<<<1, JT, 0, s>>>(m, G, Z, w, perm, max_sweeps);
+  LAUNCH_NOTE(1);
+}
+
+void jacobi32_batched(const BDesc* D, int np, int which, int k, int max_sweeps, cudaStream_t s) {
+  jacobi32_batched_kernel<<<np, JT, 0, s>>>(D, which, k, max_sweeps);
+  LAUNCH_NOTE(1);
+}
+
+void cluster_jacobi_batched(const BDesc* D, int np, int zsel, double rel, int max_sweeps, cudaStream_t s) {
+  cluster_jacobi_batched_kernel<<<np, 1024, 0, s>>>(D, zsel, rel, max_sweeps);
   LAUNCH_NOTE(1);
 }
 

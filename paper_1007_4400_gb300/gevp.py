@@ -52,6 +52,22 @@ class GevpStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GevpBatchStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("rounds", C.c_int), ("max_rounds_step", C.c_int), ("graph_replays", C.c_int),
+                ("switches", C.c_int), ("orth_fallbacks", C.c_int), ("final_passes", C.c_int),
+                ("converged", C.c_int), ("tile", C.c_int * 8), ("deg_cap", C.c_int * 8), ("max_resid", C.c_double),
+                ("flops_fp64", C.c_double), ("flops_lowp", C.c_double),
+                ("ms_chol", C.c_float), ("ms_reduce", C.c_float), ("ms_bounds", C.c_float),
+                ("ms_rounds", C.c_float), ("ms_final", C.c_float), ("ms_total", C.c_float)]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if k in ("tile", "deg_cap") else v
+        return d
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -84,6 +100,9 @@ def load(build_if_missing: bool = True):
                                           C.POINTER(GevpOpts), vp, vp, i64, vp, C.POINTER(GevpStats)]
         L.gevp_solve_sequence_host.argtypes = [vp, i32, i64, C.POINTER(vp), i64, C.POINTER(vp), i64, i32,
                                                C.POINTER(GevpOpts), vp, vp, i64, vp, C.POINTER(GevpStats)]
+        L.gevp_solve_batched.argtypes = [vp, i32, i32, vp, vp, vp, C.POINTER(vp), vp, C.POINTER(vp), vp,
+                                         C.POINTER(vp), vp, vp, C.POINTER(GevpOpts), C.POINTER(vp), C.POINTER(vp),
+                                         C.POINTER(vp), vp, C.POINTER(GevpBatchStats)]
         L.gevp_chebyshev_filter.argtypes = [vp, i64, vp, i64, vp, i64, i32, i32, f64, f64, f64, i32]
         L.gevp_cholqr2.argtypes = [vp, i64, i32, vp, i64, vp, i64]
         L.gevp_rayleigh_ritz.argtypes = [vp, i64, i32, vp, i64, vp, i64, vp, i64, vp, vp]
@@ -94,7 +113,7 @@ def load(build_if_missing: bool = True):
         L.gevp_kernel_launches.argtypes = [vp]
         L.gevp_kernel_launches.restype = i64
         for name in ("gevp_create", "gevp_destroy", "gevp_set_stream", "gevp_reduce", "gevp_solve_sequence",
-                     "gevp_solve_sequence_host", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
+                     "gevp_solve_sequence_host", "gevp_solve_batched", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
                      "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_probe_peaks"):
             getattr(L, name).restype = i32
         _LIB = L
@@ -236,6 +255,68 @@ def solve_sequence_host(A_list, B, nev: int, keep_all_X: bool = False, device=No
     if check and st not in (0, 3):
         _check(st, h)
     return SequenceResult(Lam, X, res, [s.as_dict() for s in stats], st)
+
+
+@dataclass
+class BatchedResult:
+    Lambda: list             # per k-point (nsteps, nev_k) float64
+    resid: list              # per k-point (nsteps, nev_k) float64
+    X: list                  # per k-point (n_k, nev_k) or (nsteps, n_k, nev_k) complex128
+    stats: dict
+    status: int
+
+
+def solve_batched(A, B, nev, nex=None, X_prev=None, keep_all_X: bool = False, want_X: bool = True,
+                  check: bool = True, **opts):
+    """gevp_solve_batched: A[k][l] (k-point k, step l) and B[k] CUDA complex128 tensors of
+    order n_k; nev (and nex) an int or a per-k-point list. All k-points advance in lock-step
+    rounds inside the library; returns per-k-point Lambda, resid and X."""
+    nk = len(A)
+    nsteps = len(A[0]) if nk else 0
+    if len(B) != nk or any(len(a) != nsteps for a in A):
+        raise ValueError("A must be nk lists of nsteps tensors and B a list of nk tensors")
+    nev_l = [int(nev)] * nk if isinstance(nev, int) else [int(v) for v in nev]
+    nex_l = None if nex is None else ([int(nex)] * nk if isinstance(nex, int) else [int(v) for v in nex])
+    ns = []
+    for k in range(nk):
+        _mat(B[k], f"B[{k}]")
+        nk_ = B[k].shape[0]
+        ns.append(nk_)
+        for l in range(nsteps):
+            _mat(A[k][l], f"A[{k}][{l}]")
+            if A[k][l].shape != (nk_, nk_) or A[k][l].stride(0) != A[k][0].stride(0):
+                raise ValueError(f"A[{k}] must be {nk_} x {nk_} with one leading dimension")
+    dev = B[0].device
+    h = _handle(dev)
+    o = default_opts(keep_all_X=1 if keep_all_X else 0, b_fixed=1, **opts)
+    i64a = lambda v: (C.c_int64 * nk)(*v)
+    i32a = lambda v: (C.c_int * nk)(*v)
+    Lam = [torch.empty((nsteps, nev_l[k]), dtype=torch.float64, device=dev) for k in range(nk)]
+    res = [torch.empty((nsteps, nev_l[k]), dtype=torch.float64, device=dev) for k in range(nk)]
+    Xs = None
+    if want_X:
+        Xs = [torch.empty(((nsteps, ns[k], nev_l[k]) if keep_all_X else (ns[k], nev_l[k])), dtype=torch.complex128,
+                          device=dev) for k in range(nk)]
+    Ap = (C.c_void_p * (nk * nsteps))(*[A[k][l].data_ptr() for k in range(nk) for l in range(nsteps)])
+    Bp = (C.c_void_p * nk)(*[b.data_ptr() for b in B])
+    xp = ldxp = kp = None
+    if X_prev is not None:
+        for k, x in enumerate(X_prev):
+            if x is not None:
+                _mat(x, f"X_prev[{k}]")
+        xp = (C.c_void_p * nk)(*[(x.data_ptr() if x is not None else 0) for x in X_prev])
+        ldxp = i64a([(x.stride(0) if x is not None else 0) for x in X_prev])
+        kp = i32a([(x.shape[1] if x is not None else 0) for x in X_prev])
+    stats = GevpBatchStats()
+    st = load().gevp_solve_batched(
+        h, nk, nsteps, i64a(ns), i32a(nev_l), (i32a(nex_l) if nex_l is not None else None), Ap,
+        i64a([A[k][0].stride(0) for k in range(nk)]), Bp, i64a([b.stride(0) for b in B]), xp, ldxp, kp, C.byref(o),
+        (C.c_void_p * nk)(*[t.data_ptr() for t in Lam]), (C.c_void_p * nk)(*[t.data_ptr() for t in res]),
+        ((C.c_void_p * nk)(*[t.data_ptr() for t in Xs]) if Xs is not None else None),
+        (i64a([nev_l[k] for k in range(nk)]) if Xs is not None else None), C.byref(stats))
+    if check and st not in (0, 3):
+        _check(st, h)
+    return BatchedResult(Lam, res, Xs, stats.as_dict(), st)
 
 
 def chebyshev_filter(Cm: torch.Tensor, Y: torch.Tensor, degree: int, lo: float, hi: float, s: float,

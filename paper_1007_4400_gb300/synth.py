@@ -183,6 +183,18 @@ def batched_sizes(nprob: int = 64, lo: int = 800, hi: int = 3000, config_id: int
     return out
 
 
+def kpoint_batch(nk: int = 64, nsteps: int = 10, lo: int = 800, hi: int = 3000, device="cpu",
+                 config_id: int = 3, sizes=None) -> list:
+    """The batched k-point workload: nk independent sequences (one per k-point), each built
+    like the SCF sequence (known-spectrum A_0, B fixed, A_{l+1} = A_l + 0.1 0.6^l P_l) with
+    its own seed (problem_index = k) and its own order n_k ~ U{lo..hi},
+    nev_k = round(0.06 n_k), nex_k = ceil(0.4 nev_k). ``sizes`` overrides the draw with a
+    list of (n, nev, nex)."""
+    sz = sizes if sizes is not None else batched_sizes(nk, lo, hi, config_id)
+    return [make_sequence(config_id, n, nsteps, nev, nex, device=device, problem_index=k)
+            for k, (n, nev, nex) in enumerate(sz)]
+
+
 def random_block(n: int, m: int, seed: int, device="cpu") -> torch.Tensor:
     """Seeded complex normal n x m block (row-major), for kernel-level tests."""
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 7 + seed))

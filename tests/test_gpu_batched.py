@@ -1,0 +1,137 @@
+"""Parity of the batched k-point entry point (gevp_solve_batched) with the FP64 oracle:
+a ragged batch of warm-started sequences solved in lock-step rounds, every k-point and
+step checked (eigenvalues, original-space residuals, B-orthonormality), agreement with
+the one-sequence solver, reuse of the captured round graph, the autotuner's outputs, and
+errors. The full-size batch (64 k-points, n in [800, 3000]) is checked on sampled
+problems by the oracle and on every problem by its residuals (slow)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+TOL_RES = 1e-10
+TOL_LAM = 1e-12
+
+SMALL = [(150, 9, 4), (203, 12, 5), (261, 16, 7), (317, 19, 8), (390, 23, 10)]
+
+
+def _batch(sizes, nsteps, device):
+    from paper_1007_4400_gb300 import synth
+    return synth.kpoint_batch(len(sizes), nsteps, device=device, sizes=sizes)
+
+
+def _solve(seqs, prec, **kw):
+    from paper_1007_4400_gb300 import gevp
+    return gevp.solve_batched([s.A for s in seqs], [s.B for s in seqs], [s.nev for s in seqs],
+                              nex=[s.nex for s in seqs], filter_prec=prec, **kw)
+
+
+def _check_kpoint(orc, seq, lam, res, X_last, keep_steps=None):
+    B = seq.B.cpu().numpy()
+    nev = seq.nev
+    steps = range(len(seq.A)) if keep_steps is None else keep_steps
+    for l in steps:
+        A = seq.A[l].cpu().numpy()
+        lam_r, _ = orc.solve(A, B, nev, method="jacobi")
+        scale = np.abs(lam_r).max()
+        assert np.abs(lam[l] - lam_r).max() <= TOL_LAM * scale, (seq.n, l)
+        assert res[l].max() <= TOL_RES, (seq.n, l, res[l].max())
+    if X_last is not None:
+        l = len(seq.A) - 1
+        A = seq.A[l].cpu().numpy()
+        nA = orc.norm2_hermitian(A)
+        assert orc.residuals(A, B, lam[l], X_last, nA).max() <= TOL_RES
+        assert np.abs(X_last.conj().T @ B @ X_last - np.eye(nev)).max() < 1e-10
+    if keep_steps is None:
+        assert np.abs(lam[0] - seq.lam0[:nev]).max() <= TOL_LAM * np.abs(seq.lam0).max()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ragged_batch_matches_oracle(cuda, orc, prec):
+    seqs = _batch(SMALL, 3, cuda)
+    r = _solve(seqs, prec)
+    assert r.status == 0, r.stats
+    st = r.stats
+    assert st["converged"] == 1 and st["max_resid"] <= TOL_RES
+    for k, s in enumerate(seqs):
+        _check_kpoint(orc, s, r.Lambda[k].cpu().numpy(), r.resid[k].cpu().numpy(), r.X[k].cpu().numpy())
+
+
+def test_batched_agrees_with_sequence_solver(cuda):
+    from paper_1007_4400_gb300 import gevp
+    seqs = _batch(SMALL[:3], 3, cuda)
+    rb = _solve(seqs, "fp32")
+    assert rb.status == 0
+    for k, s in enumerate(seqs):
+        rs = gevp.solve_sequence(s.A, s.B, s.nev, nex=s.nex, filter_prec="fp32")
+        assert rs.status == 0
+        lb, ls = rb.Lambda[k].cpu().numpy(), rs.Lambda.cpu().numpy()
+        assert np.abs(lb - ls).max() <= 2 * TOL_LAM * np.abs(ls).max()
+
+
+def test_graph_reuse_and_autotuner(cuda):
+    """A second call with the same shapes replays the captured round (no new tuning), the
+    tile choices are valid, and the degree caps lie in [deg_min, deg_max]."""
+    seqs = _batch(SMALL, 4, cuda)
+    r1 = _solve(seqs, "fp32", deg_min=4, deg_max=24)
+    r2 = _solve(seqs, "fp32", deg_min=4, deg_max=24)
+    assert r1.status == 0 and r2.status == 0
+    assert r2.stats["graph_replays"] == r2.stats["rounds"] >= 1
+    assert all(t in (0, 32, 64) for t in r2.stats["tile"])
+    assert all(4 <= d <= 24 for d in r2.stats["deg_cap"])
+    for k in range(len(seqs)):
+        a, b = r1.Lambda[k].cpu().numpy(), r2.Lambda[k].cpu().numpy()
+        assert np.abs(a - b).max() <= TOL_LAM * np.abs(a).max()
+
+
+def test_keep_all_X_and_caller_start(cuda, orc):
+    """Every step's eigenvectors (keep_all_X) and a caller-supplied start block for step 0."""
+    seqs = _batch(SMALL[:2], 2, cuda)
+    X0 = []
+    for s in seqs:
+        lam, X = orc.solve(s.A[0].cpu().numpy(), s.B.cpu().numpy(), s.nev, method="jacobi")
+        X0.append(torch.from_numpy(X).to(cuda))
+    r = _solve(seqs, "fp32", keep_all_X=True, X_prev=X0)
+    assert r.status == 0
+    for k, s in enumerate(seqs):
+        B = s.B.cpu().numpy()
+        for l in range(2):
+            X = r.X[k][l].cpu().numpy()
+            A = s.A[l].cpu().numpy()
+            lam = r.Lambda[k][l].cpu().numpy()
+            assert orc.residuals(A, B, lam, X, orc.norm2_hermitian(A)).max() <= TOL_RES
+            assert np.abs(X.conj().T @ B @ X - np.eye(s.nev)).max() < 1e-10
+
+
+def test_batched_errors(cuda):
+    from paper_1007_4400_gb300 import gevp
+    seqs = _batch(SMALL[:2], 1, cuda)
+    Bbad = seqs[1].B.clone()
+    Bbad[3, 3] = -5.0
+    with pytest.raises(gevp.GevpError) as e:
+        gevp.solve_batched([s.A for s in seqs], [seqs[0].B, Bbad], [s.nev for s in seqs])
+    assert e.value.status == 2
+    with pytest.raises(gevp.GevpError) as e:
+        gevp.solve_batched([s.A for s in seqs], [s.B for s in seqs], [s.n + 1 for s in seqs])
+    assert e.value.status == 1
+
+
+@pytest.mark.slow
+def test_full_size_kpoint_batch(cuda, orc):
+    """64 k-points, n ~ U{800..3000}, nev = round(0.06 n), two warm steps, FP32-class filter:
+    every residual <= tol; the oracle's eigenvalues on the two smallest k-points."""
+    from paper_1007_4400_gb300 import synth
+    sizes = synth.batched_sizes(64)
+    seqs = synth.kpoint_batch(64, 2, device=cuda, sizes=sizes)
+    r = _solve(seqs, "fp32", want_X=False)
+    assert r.status == 0, r.stats
+    for k in range(64):
+        assert r.resid[k].max().item() <= TOL_RES
+    order = np.argsort([n for n, _, _ in sizes])[:2]
+    for k in order:
+        s = seqs[k]
+        lam_r, _ = orc.solve(s.A[1].cpu().numpy(), s.B.cpu().numpy(), s.nev, method="tridiag")
+        assert np.abs(r.Lambda[k][1].cpu().numpy() - lam_r).max() <= TOL_LAM * np.abs(lam_r).max()
