@@ -46,7 +46,7 @@ def parse():
                    help="where the synthetic inputs are generated (cpu for runs under ncu)")
     p.add_argument("--kpoints", type=int, default=64, help="kpoint_batch workload: number of k-points")
     p.add_argument("--seq-steps", type=int, default=10, help="kpoint_batch workload: problems per k-point")
-    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce"], default=None,
+    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched"], default=None,
                    help="run only a few launches of one kernel (n 2048, m 140) for ncu captures")
     return p.parse_args()
 
@@ -56,6 +56,17 @@ def kernel_case(args):
     import torch
     from paper_1007_4400_gb300 import gevp, synth
     dev = torch.device("cuda", 0)
+    if args.kernel_case == "batched":
+        # one step of a small k-point batch (inputs built on the host), FP32-class filter:
+        # the grouped tcgen05 filter, grouped FP64 GEMMs and the batched small kernels
+        seqs = synth.kpoint_batch(args.kpoints, 1, device="cpu")
+        A = [[a.to(dev) for a in s.A] for s in seqs]
+        B = [s.B.to(dev) for s in seqs]
+        r = gevp.solve_batched(A, B, [s.nev for s in seqs], nex=[s.nex for s in seqs], filter_prec="fp32",
+                               want_X=False)
+        torch.cuda.synchronize()
+        print(f"kernel case batched done: {len(seqs)} k-points, status {r.status}, rounds {r.stats['rounds']}")
+        return 0
     kw = synth.WORKLOADS[args.workload]
     n, m = kw["n"], kw["nev"] + kw["nex"]
     # a random Hermitian matrix of the workload's size and scale (no factorisations, so the
@@ -234,17 +245,25 @@ def bench_batched(args):
     """The batched form: nk k-points (n ~ U{800..3000}, nev = round(0.06 n)), each a warm
     sequence of seq_steps problems, all solved by one gevp_solve_batched call per step."""
     import torch
-    from paper_1007_4400_gb300 import gevp, synth
+    from paper_1007_4400_gb300 import gevp, shard, synth
     rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    seqs = synth.kpoint_batch(args.kpoints, args.seq_steps, device=dev)
+    # k-points are independent: each rank solves a cost-balanced subset (no collective on
+    # the data path; only the timings are reduced)
+    sizes_all = synth.batched_sizes(args.kpoints)
+    mine = shard.shard_kpoints(sizes_all, world)[rank]
+    seqs = [synth.make_sequence(3, sizes_all[k][0], args.seq_steps, sizes_all[k][1], sizes_all[k][2], device=dev,
+                                problem_index=k) for k in mine]
     A = [s.A for s in seqs]
     B = [s.B for s in seqs]
     nev = [s.nev for s in seqs]
     nex = [s.nex for s in seqs]
-    nominal = sum(args.seq_steps * nominal_flops_per_problem(s.n, s.nev + s.nex, s.nev, args.seq_steps)
-                  for s in seqs)
+    nominal = sum(args.seq_steps * nominal_flops_per_problem(n, ne + nx, ne, args.seq_steps)
+                  for n, ne, nx in sizes_all)
 
     def step(**kw):
         o = dict(filter_prec=args.prec)
@@ -257,6 +276,8 @@ def bench_batched(args):
     launches0 = gevp.kernel_launches(local)
     clocks = ClockSampler(local)
     clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -264,13 +285,14 @@ def bench_batched(args):
     results = [step() for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
+    barrier(world)
     clk = clocks.stop()
     launches = (gevp.kernel_launches(local) - launches0) // max(1, args.steps)
-    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     r = results[-1]
-    maxres = max(float(t.max()) for t in r.resid)
+    maxres = max_over_ranks(max(float(t.max()) for t in r.resid), world, dev)
     compare = None
-    if not args.no_compare:
+    if not args.no_compare and world == 1:
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         c0.record(stream)
@@ -282,12 +304,18 @@ def bench_batched(args):
                    "batched_fp64_cold_resid_max": max(float(t.max()) for t in rc.resid),
                    "batched_fp64_cold_rounds": rc.stats["rounds"]}
     nprob = args.kpoints * args.seq_steps
-    out = {"metric": METRIC, "value": nominal / (ms_step * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    out = {"metric": METRIC, "value": nominal / (ms_step * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.prec == "fp64" else f"f64+{args.prec}", "data": "synthetic",
            "config": {"workload": "kpoint_batch", "kpoints": args.kpoints, "problems_per_kpoint": args.seq_steps,
-                      "n_range": [min(s.n for s in seqs), max(s.n for s in seqs)],
+                      "n_range": [min(x[0] for x in sizes_all), max(x[0] for x in sizes_all)],
+                      "parallelism": f"k-points sharded over {world} GPU(s)" if world > 1 else "single GPU",
                       "nev": "round(0.06 n)", "nex": "ceil(0.4 nev)", "filter_prec": args.prec,
                       "start": "warm within each k-point", "l2": "inputs larger than L2"},
            "problems_per_s": nprob / (ms_step * 1e-3), "converged": all(x.status == 0 for x in results),
@@ -295,6 +323,9 @@ def bench_batched(args):
            "gpu_launches_note": "host-enqueued launches; graph replays are counted in stats.graph_replays",
            "compare": compare}
     print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 

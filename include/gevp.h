@@ -91,7 +91,7 @@ typedef struct {
   float ms_chol, ms_reduce, ms_bounds, ms_filter, ms_orth, ms_rr, ms_resid, ms_final, ms_total;
 } gevp_stats;
 
-/* Fills *o with the defaults: FP64 filter, tol 1e-10, max_outer 60, degrees 4..24,
+/* Fills *o with the defaults: FP64 filter, tol 1e-10, max_outer 60, degrees 4..48,
  * nex 0 (callers set it), seed 10074400, b_fixed 0, cold_start 0, lanczos_steps 32,
  * refine_iters 3, keep_all_X 0. */
 void gevp_default_opts(gevp_opts* o);

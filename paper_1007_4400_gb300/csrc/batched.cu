@@ -503,7 +503,7 @@ void enqueue_rr(BatchPlan* P, cudaStream_t s, bool tune) {
   launch(P, P->c_Ef[zsel], s, tune);
   launch(P, P->c_Sf[zsel], s, tune);
   bk_hermitize_avg_S(P->dD, np, mmax, s);
-  cluster_jacobi_batched(P->dD, np, zsel, 1e-15, 6, s);
+  cluster_jacobi_batched(P->dD, np, zsel, 1e-15, 12, s);
   bk_sort_pairs(P->dD, np, zsel, s);
   launch(P, P->c_qz, s, tune);
   bk_copy_nm(P->dD, np, P->nmax * mmax, 0, 2, s);   // Q <- Y1
@@ -706,8 +706,8 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
   for (int k = 0; k < np; ++k) {
     BDesc& d = P->hD[k];
     zcopy2d(n[k], n[k], (const double2*)B[k], ldb[k], d.L, n[k], s);
-    potrf_lower(n[k], d.L, n[k], P->dInfo + k, nullptr, 0, s);
-    trtri_lower(n[k], d.L, n[k], d.Linv, n[k], P->trtri_ws, P->trtri_elems, s);
+    potrf_lower(n[k], d.L, n[k], P->dInfo + k, d.Linv, n[k], s);
+    trtri_lower(n[k], d.L, n[k], d.Linv, n[k], P->trtri_ws, P->trtri_elems, s, true);
   }
   BCK(cudaMemcpyAsync(P->hInfo, P->dInfo, np * sizeof(int), cudaMemcpyDeviceToHost, s));
   BCK(cudaEventRecord(evt(P, EV_CHOL), s));

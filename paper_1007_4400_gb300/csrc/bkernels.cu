@@ -11,12 +11,13 @@
 //   [17] tolerance in the original space         [18] largest residual of this round
 //   [19] largest residual at the start of the step
 //   [20] Chebyshev convergence factor of the nev-th Ritz value
+//   [21] largest residual predicted for the end of this round
 // Per-problem flags, BDesc::flags (int):
 //   [0] active (rounds still run)  [1] filter degree of this round  [2] Cholesky info
 //   [3] state: 0 iterating, 1 converged in the standard space (final check pending),
 //       2 done, 3 gave up   [4] rounds  [5] FP64 filter  [6] tensor-core filter runs
 //   [7] FP64 filter runs  [8] CholQR failures  [9] filter steps  [10] precision switches
-//   [11] final passes  [12] final check runs
+//   [11] final passes  [12] final check runs  [13] degree cap after filter stalls
 #include "gevp_internal.cuh"
 #include <algorithm>
 
@@ -389,6 +390,7 @@ __global__ void b_step_reset(const BDesc* D, int np, double tol, int filter64) {
   for (int i = 0; i < 16; ++i) d.flags[i] = 0;
   d.flags[0] = 1;
   d.flags[5] = filter64;
+  d.flags[13] = kBDegMax;
   d.bounds[8] = 1e300;
   d.bounds[17] = tol;
 }
@@ -672,7 +674,7 @@ __global__ void __launch_bounds__(256) b_cheb_coef(const BDesc* D, int deg_min, 
     return;
   }
   const int m = d.m, nev = d.nev;
-  const int cap = max(deg_min, min(deg_cap[blockIdx.x], kBDegMax));
+  const int cap = max(deg_min, min(min(deg_cap[blockIdx.x], d.flags[13]), kBDegMax));
   if (threadIdx.x == 0) {
     double hi = d.bounds[2];
     double lo = d.theta[m - 1];
@@ -698,8 +700,19 @@ __global__ void __launch_bounds__(256) b_cheb_coef(const BDesc* D, int deg_min, 
     }
   }
   need = bmax_d(need, red);
+  const int deg = (int)fmin(fmax(need, (double)deg_min), (double)cap);
+  // largest residual Chebyshev theory predicts after this round (|T_deg(t_i)| gain for
+  // every unconverged wanted pair outside the damped interval)
+  double pred = 0.0;
+  for (int i = threadIdx.x; i < nev; i += blockDim.x) {
+    double r = d.res[i];
+    const double at = fabs((d.theta[i] - c) / e);
+    if (r > tolC && at > 1.0) r /= cosh(deg * acosh(fmin(at, 1e150)));
+    pred = fmax(pred, r == r ? r : 1e300);
+  }
+  pred = bmax_d(pred, red);
   if (threadIdx.x == 0) {
-    int deg = (int)fmin(fmax(need, (double)deg_min), (double)cap);
+    d.bounds[21] = pred;
     s_deg = deg;
     d.flags[1] = deg;
     d.flags[2] = 0;
@@ -727,7 +740,6 @@ __global__ void __launch_bounds__(256) b_cheb_coef(const BDesc* D, int deg_min, 
     }
   }
   __syncthreads();
-  const int deg = s_deg;
   if (threadIdx.x < kBDegMax) d.stepact[threadIdx.x] = (d.flags[7] && (int)threadIdx.x < deg) ? 1 : 0;
   if (d.pcoef) {
     // scalar recurrence at each Ritz value: pcoef[j][col] = alpha_j p_j(theta), pfinal = p_deg(theta)
@@ -793,9 +805,17 @@ __global__ void b_round_status(const BDesc* D, int* out) {
       d.flags[3] = 1;
       d.flags[0] = 0;
       d.flags[12] = 1;
-    } else if (!info && !d.flags[5] && mx > 0.25 * d.bounds[8] && d.bounds[8] < 1e300) {
-      d.flags[5] = 1;
-      d.flags[10] += 1;
+    } else if (!info && !d.flags[5] && mx > 0.25 * d.bounds[8] && d.bounds[8] < 1e300 &&
+               mx > 25.0 * d.bounds[21]) {
+      // the low-precision filter gained less than 4x where the Chebyshev factors of this
+      // round promised more than 100x: it has reached its floor. The FP32-class floor
+      // depends on the degree, so its cap is halved first (down to 16); BF16 -> FP64.
+      if (d.nsplit == 3 && d.flags[13] > 16) {
+        d.flags[13] = max(16, d.flags[13] / 2);
+      } else {
+        d.flags[5] = 1;
+        d.flags[10] += 1;
+      }
     }
     d.bounds[8] = mx;
     out[p] = d.flags[0] | (info ? 2 : 0);
@@ -915,14 +935,14 @@ void bk_lanczos(const BDesc* D, int np, int64_t nmax, int k, int use_count, int 
   }
   b_build_T<<<np, 256, 0, s>>>(D, k);
   LAUNCH_NOTE(1);
-  jacobi32_batched(D, np, 1, k, 30, s);
+  jacobi32_batched(D, np, 1, k, k, 30, s);
   b_lanczos_finish<<<np, 32, 0, s>>>(D, k, use_count, out_off);
   LAUNCH_NOTE(1);
 }
 void bk_heev_prep(const BDesc* D, int np, int mmax, cudaStream_t s) {
   b_g_to_c<<<g2((int64_t)mmax * mmax, np), 256, 0, s>>>(D);
   LAUNCH_NOTE(1);
-  jacobi32_batched(D, np, 0, 0, 40, s);
+  jacobi32_batched(D, np, 0, 0, mmax, 40, s);
   b_gather_z<<<g2((int64_t)mmax * mmax, np), 256, 0, s>>>(D);
   b_frob<<<np, 1024, 0, s>>>(D);
   LAUNCH_NOTE(2);

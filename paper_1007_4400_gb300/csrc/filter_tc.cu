@@ -144,7 +144,9 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* amaps, const CUtensor
   const int kb0 = z * p.kb_per_split;
   const int kb1 = min(kb0 + p.kb_per_split, nkb_total);
   const int nkb = max(0, kb1 - kb0);
-  const int niter = nkb * p.nseg;     // segment-major: all K blocks of segment 0, then 1, ...
+  // K-block-major: all segments of one K block back to back, so the C piece a segment
+  // reloads (piece 0 serves three segments, piece 1 two) is still in L2
+  const int niter = nkb * p.nseg;
   const uint32_t a_bytes = TM * TK * 2;
   const uint32_t b_bytes = (uint32_t)p.nchunk * TK * 2;
   const uint32_t stage_bytes = 3 * a_bytes + 3 * b_bytes;
@@ -177,8 +179,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* amaps, const CUtensor
       uint32_t ph = (uint32_t)(i / STAGES) & 1u;
       if (i >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, p.err, 1)) break;
       mbar_expect_tx(&full[s], stage_bytes);
-      const int seg = i / nkb;
-      const int kx = (kb0 + i % nkb) * TK;
+      const int seg = i % p.nseg;
+      const int kx = (kb0 + i / p.nseg) * TK;
       const CUtensorMap* A = amaps + 3 * kSegA[seg];
       const CUtensorMap* B = bmaps + 3 * kSegB[seg];
       tma_load_2d(tile(s, 0), A + 0, kx, m0, &full[s]);

@@ -70,6 +70,20 @@ struct gevp_ctx {
   std::string err;
   gevp::FilterTC* tc = nullptr;
   gevp::BatchPlan* batch = nullptr;   // state of the batched (k-point) entry point
+  // sequence pipelining: the solver runs on a high-priority internal stream while a
+  // low-priority side stream builds the next problem's standard form into a second set
+  // of buffers (C2, its FP32 copy and bounds, the tensor-core planes in tc2)
+  cudaStream_t hi = nullptr, side = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_side = nullptr, ev_user = nullptr;
+  char* parena = nullptr;
+  size_t parena_bytes = 0;
+  double2 *C2 = nullptr, *T2 = nullptr, *split2 = nullptr;
+  size_t split2_elems = 0;
+  float2* M32b = nullptr;
+  LanczosWork lw2{};
+  double* bounds2 = nullptr;   // device: [0..4] bounds of C, [8..12] of A
+  double* hb2 = nullptr;       // pinned copy
+  gevp::FilterTC* tc2 = nullptr;
 };
 
 namespace gevp {
@@ -148,7 +162,7 @@ size_t layout(gevp_ctx* h, char* base, int64_t n, int m) {
   h->hw.T = (double2*)take(mm * 16);
   h->hw.E = (double2*)take(mm * 16);
   h->hw.lam = (double*)take(m * 8 + 64);
-  h->hw.scal = (double*)take(16 * 8);
+  h->hw.scal = (double*)take(16 * 8 + 64 * 4);   // 16 scalars, then 64 floats of Jacobi reductions
   h->hw.split_ws = h->split;
   h->hw.split_ws_elems = h->split_elems;
   // lanczos (KMAX = 64)
@@ -260,7 +274,7 @@ gevp_status sync_read(gevp_ctx* h, const void* dsrc, void* hdst, size_t bytes) {
 gevp_status factor_B(gevp_ctx* h, int64_t n, const double2* B, int64_t ldb, int64_t* info_out) {
   CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
   zcopy2d(n, n, B, ldb, h->L, n, h->stream);
-  potrf_lower(n, h->L, n, h->info, nullptr, 0, h->stream);
+  potrf_lower(n, h->L, n, h->info, h->Linv, n, h->stream);
   int info = 0;
   TRY(sync_read(h, h->info, &info, sizeof(int)));
   if (info_out) *info_out = info;
@@ -271,22 +285,80 @@ gevp_status factor_B(gevp_ctx* h, int64_t n, const double2* B, int64_t ldb, int6
     h->err = buf;
     return GEVP_ERR_NOT_HPD;
   }
-  trtri_lower(n, h->L, n, h->Linv, n, h->trtri_ws, h->trtri_elems, h->stream);
+  trtri_lower(n, h->L, n, h->Linv, n, h->trtri_ws, h->trtri_elems, h->stream, true);
   h->chol_valid = true;
   return GEVP_OK;
 }
 
-// C = Linv A Linv^H into Cout (n x n, ld ldc), via T = Linv tril_half(A), M = T Linv^H.
-void reduce_into(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, double2* Cout, int64_t ldc) {
-  ZgemmArgs a = zg((int)n, (int)n, (int)n, h->Linv, n, 0, A, lda, 0, h->T, n);
+// C = Linv A Linv^H into Cout (n x n, ld ldc), via T = Linv tril_half(A), M = T Linv^H,
+// with the given scratch (T, split-K) on the given stream.
+void reduce_into_ws(int64_t n, const double2* Linv, const double2* A, int64_t lda, double2* Cout, int64_t ldc,
+                    double2* T, double2* split, size_t split_elems, cudaStream_t s) {
+  ZgemmArgs a = zg((int)n, (int)n, (int)n, Linv, n, 0, A, lda, 0, T, n);
   a.triA = 1;
   a.maskB = 1;
-  zgemm(a, h->split, h->split_elems, h->stream);
-  ZgemmArgs b = zg((int)n, (int)n, (int)n, h->T, n, 0, h->Linv, n, 1, Cout, ldc);
+  zgemm(a, split, split_elems, s);
+  ZgemmArgs b = zg((int)n, (int)n, (int)n, T, n, 0, Linv, n, 1, Cout, ldc);
   b.triA = 1;
   b.triB = 2;
-  zgemm(b, h->split, h->split_elems, h->stream);
-  herm_sum_inplace(n, Cout, ldc, h->stream);
+  zgemm(b, split, split_elems, s);
+  herm_sum_inplace(n, Cout, ldc, s);
+}
+
+void reduce_into(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, double2* Cout, int64_t ldc) {
+  reduce_into_ws(n, h->Linv, A, lda, Cout, ldc, h->T, h->split, h->split_elems, h->stream);
+}
+
+// Streams and buffers of the sequence pipeline (sized from the main arena's n and split).
+gevp_status ensure_pipeline(gevp_ctx* h) {
+  if (!h->hi) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, greatest));
+    CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, least));
+    CK(cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming));
+  }
+  if (!h->hb2) CK(cudaMallocHost(&h->hb2, 24 * sizeof(double)));
+  const int64_t n = h->cap_n;
+  auto lay = [&](char* base) -> size_t {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+      char* p = base ? base + off : nullptr;
+      off += al(bytes);
+      return p;
+    };
+    h->C2 = (double2*)take((size_t)n * n * 16);
+    h->T2 = (double2*)take((size_t)n * n * 16);
+    h->M32b = (float2*)take((size_t)n * n * 8);
+    h->split2 = (double2*)take(h->split_elems * 16);
+    h->lw2.V = (float2*)take((size_t)65 * n * 8);
+    h->lw2.ab = (float*)take(140 * 4);
+    h->lw2.w = (float2*)take((size_t)n * 8);
+    h->lw2.T32 = (float2*)take(64 * 64 * 8);
+    h->lw2.Z32 = (float2*)take(64 * 64 * 8);
+    h->lw2.w32 = (float*)take(64 * 4);
+    h->lw2.perm = (int*)take(64 * 4);
+    h->lw2.out = nullptr;
+    h->bounds2 = (double*)take(24 * 8);
+    return off;
+  };
+  const size_t need = lay(nullptr);
+  if (!h->parena || need > h->parena_bytes) {
+    if (h->parena) {
+      cudaStreamSynchronize(h->side);
+      cudaFree(h->parena);
+      h->parena = nullptr;
+    }
+    void* p = nullptr;
+    CK(cudaMalloc(&p, need));
+    h->parena = (char*)p;
+    h->parena_bytes = need;
+  }
+  lay(h->parena);
+  h->split2_elems = h->split_elems;
+  return GEVP_OK;
 }
 
 // Orthonormalise Y (n x ma, ld ldy) against Q[:, 0:nlock] and by CholQR2; result in Out.
@@ -327,7 +399,7 @@ gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_
           zshift_diag(ma, h->Gw, ma, sh, h->stream);
         }
         CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
-        potrf_lower(ma, h->Gw, ma, h->info, nullptr, 0, h->stream);
+        potrf_lower(ma, h->Gw, ma, h->info, h->Gwi, ma, h->stream);
         int info = 0;
         TRY(sync_read(h, h->info, &info, sizeof(int)));
         if (info == 0) break;
@@ -336,7 +408,7 @@ gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_
       }
       if (attempt == 3) { failed = true; break; }
       plain_ok = shifted ? 0 : plain_ok + 1;
-      trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream);
+      trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream, true);
       zcol_scale(n, ma, src, lds, h->dscale, h->stream);
       ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
       q.triB = 2;
@@ -437,11 +509,26 @@ int choose_degree(const SolveState& S, double lo, double hi, double tolC, int dm
   return std::min(std::max(d, dmin), dmax);
 }
 
+// Largest residual among the unlocked wanted pairs that Chebyshev theory predicts after a
+// filter of degree deg: an unconverged pair's residual shrinks by |T_deg(t_i)| (t_i its
+// Ritz value mapped to the damped interval; no gain when |t_i| <= 1).
+double predicted_max_res(const SolveState& S, double lo, double hi, double tolC, int deg) {
+  double e = 0.5 * (hi - lo), c = 0.5 * (hi + lo), pred = 0.0;
+  for (int i = S.nlock; i < S.nev; ++i) {
+    double r = S.res[i];
+    double at = std::fabs((S.theta[i] - c) / e);
+    if (r > tolC && at > 1.0) r /= std::cosh(deg * std::acosh(std::min(at, 1e150)));
+    pred = std::max(pred, r);
+  }
+  return pred;
+}
+
 // Solve one problem whose standard form is already in h->C. Q holds the start block
 // (orthonormal, all m columns) when warm; otherwise it is drawn here.
 gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, const double2* B, int64_t ldb,
                       int nev, int m, bool warm, const gevp_opts& o, int prob_index, Timer& tm, gevp_stats* st,
-                      double* Lam_out, double2* X_out, int64_t ldx, double* res_out) {
+                      double* Lam_out, double2* X_out, int64_t ldx, double* res_out, const double* pre = nullptr,
+                      bool tc_ready = false) {
   const int64_t ld = h->cap_m;
   SolveState S;
   S.m = m;
@@ -449,17 +536,20 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   S.theta.assign(m, 0.0);
   S.res.assign(m, 0.0);
   double hb[16];
-  // bounds of C, and an estimate of ||A||_2 for the final residuals
-  TRY(lanczos(h, n, h->C, n, o.lanczos_steps, m, o.seed + 7919ull * prob_index, hb));
+  // bounds of C, and an estimate of ||A||_2 for the final residuals (pre: computed ahead
+  // on the side stream, by the same kernels with the same seeds)
+  if (pre) std::memcpy(hb, pre, 5 * sizeof(double));
+  else TRY(lanczos(h, n, h->C, n, o.lanczos_steps, m, o.seed + 7919ull * prob_index, hb));
   S.lower_est = hb[0];
   S.upper = hb[2];
   S.a_est = hb[3];
   S.normC = std::max(std::fabs(hb[0]), std::fabs(hb[2]));
-  TRY(lanczos(h, n, A, lda, o.lanczos_steps, 0, o.seed + 104729ull * prob_index + 1, hb));
+  if (pre) std::memcpy(hb, pre + 8, 5 * sizeof(double));
+  else TRY(lanczos(h, n, A, lda, o.lanczos_steps, 0, o.seed + 104729ull * prob_index + 1, hb));
   S.normA = std::max(std::fabs(hb[0]), std::fabs(hb[1]));
   int prec = o.filter_prec;
   const int nsplit = (prec == GEVP_PREC_FP32) ? 3 : 1;
-  if (prec != GEVP_PREC_FP64) {
+  if (prec != GEVP_PREC_FP64 && !tc_ready) {
     CK(filter_tc_reserve(&h->tc, n, m));
     CK(filter_tc_set_matrix(h->tc, n, h->C, n, nsplit, h->stream));
   }
@@ -481,6 +571,7 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   int final_pass = 0;
   double prev_maxres = 1e300;
   bool converged = false;
+  int deg_cap = o.deg_max;   // lowered when the FP32-class filter reaches its floor
   for (int it = 0;; ++it) {
     if (S.have_theta) {
       while (S.nlock < nev && S.res[S.nlock] <= tolC) S.nlock++;
@@ -504,8 +595,9 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
       double mx = 0;
       int first_bad = nev;
       for (int i = 0; i < nev; ++i) {
-        mx = std::max(mx, rf[i]);
-        if (rf[i] > o.tol && first_bad == nev) first_bad = i;
+        // a NaN residual fails (and is reported): every comparison with NaN is false
+        if (!(rf[i] <= mx)) mx = rf[i];
+        if (!(rf[i] <= o.tol) && first_bad == nev) first_bad = i;
       }
       if (st) { st->final_passes = final_pass; st->max_resid = mx; }
       if (first_bad == nev) { converged = true; break; }
@@ -525,7 +617,8 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     double sc = S.have_theta ? std::min(S.theta[0], S.lower_est) : S.lower_est;
     if (!(lo > sc + 1e-3 * (hi - sc))) lo = sc + 0.5 * (hi - sc);
     if (!(hi > lo)) hi = lo + 1e-3 * S.normC + 1e-300;
-    int deg = S.have_theta ? choose_degree(S, lo, hi, tolC, o.deg_min, o.deg_max) : std::min(o.deg_max, 10);
+    int deg = S.have_theta ? choose_degree(S, lo, hi, tolC, o.deg_min, deg_cap) : std::min(deg_cap, 10);
+    const double pred = S.have_theta ? predicted_max_res(S, lo, hi, tolC, deg) : 0.0;
     double2* Yf;
     if (prec != GEVP_PREC_FP64) {
       if (S.have_theta) {
@@ -559,11 +652,20 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     if (st) st->outer_iters++;
     double mr = 0;
     for (int i = S.nlock; i < nev; ++i) mr = std::max(mr, S.res[i]);
-    // precision switch: the low-precision filter has stalled (less than 4x progress in a
-    // round) or the residuals reached its floor -> FP64 for the rest of this problem
-    if (prec != GEVP_PREC_FP64 && mr > 0.25 * prev_maxres) {
-      prec = GEVP_PREC_FP64;
-      if (st) st->switches++;
+    // precision switch: the low-precision filter has reached its floor (less than 4x
+    // progress in a round where the Chebyshev factors promised more than 100x) -> FP64
+    // for the rest of this problem. Slow progress that theory predicts (Ritz values close
+    // to the damped interval) is no reason to switch: FP64 would not converge faster.
+    if (prec != GEVP_PREC_FP64 && mr > 0.25 * prev_maxres && (pred <= 0.0 || mr > 25.0 * pred)) {
+      // The FP32-class filter's floor depends on the degree (its rounding is amplified
+      // along the recurrence): first halve the degree cap, down to 16; BF16's floor does
+      // not depend on it, so BF16 switches at once.
+      if (prec == GEVP_PREC_FP32 && deg_cap > 16) {
+        deg_cap = std::max(16, deg_cap / 2);
+      } else {
+        prec = GEVP_PREC_FP64;
+        if (st) st->switches++;
+      }
     }
     prev_maxres = mr;
   }
@@ -588,6 +690,54 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
 
 bool bad_ld(int64_t ld, int64_t cols) { return ld < cols || ld <= 0; }
 
+// Standard form, spectral bounds and tensor-core planes of problem idx (matrix A) on the
+// side stream into C2 / bounds2 / tc2, ordered after everything already enqueued on the
+// main stream (which includes the last use of those buffers by the problem before). The
+// kernels and seeds are those of the main path, so the results are identical.
+gevp_status prefetch_problem(gevp_ctx* h, int64_t n, int m, const double2* A, int64_t lda, const gevp_opts& o,
+                             int idx) {
+  CK(cudaEventRecord(h->ev_main, h->stream));
+  CK(cudaStreamWaitEvent(h->side, h->ev_main, 0));
+  reduce_into_ws(n, h->Linv, A, lda, h->C2, n, h->T2, h->split2, h->split2_elems, h->side);
+  z_to_c(n, n, h->C2, n, h->M32b, n, h->side);
+  lanczos_bounds(n, h->M32b, n, o.lanczos_steps, m, o.seed + 7919ull * idx, h->lw2, h->bounds2, h->side);
+  z_to_c(n, n, A, lda, h->M32b, n, h->side);
+  lanczos_bounds(n, h->M32b, n, o.lanczos_steps, 0, o.seed + 104729ull * idx + 1, h->lw2, h->bounds2 + 8, h->side);
+  CK(cudaMemcpyAsync(h->hb2, h->bounds2, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->side));
+  if (o.filter_prec != GEVP_PREC_FP64) {
+    CK(filter_tc_reserve(&h->tc2, n, m));
+    CK(filter_tc_set_matrix(h->tc2, n, h->C2, n, o.filter_prec == GEVP_PREC_FP32 ? 3 : 1, h->side));
+  }
+  CK(cudaEventRecord(h->ev_side, h->side));
+  return GEVP_OK;
+}
+
+// For the duration of a sequence solve: work on the internal high-priority stream (after
+// the caller's stream), and on every exit hand back to the caller's stream, wait for the
+// side stream and give the double-buffered standard form its original roles.
+struct PipelineScope {
+  gevp_ctx* h;
+  cudaStream_t user;
+  bool swapped = false;
+  PipelineScope(gevp_ctx* hh) : h(hh), user(hh->stream) {
+    cudaEventRecord(h->ev_user, user);
+    cudaStreamWaitEvent(h->hi, h->ev_user, 0);
+    h->stream = h->hi;
+  }
+  void swap_buffers() {
+    std::swap(h->C, h->C2);
+    std::swap(h->tc, h->tc2);
+    swapped = !swapped;
+  }
+  ~PipelineScope() {
+    cudaStreamSynchronize(h->side);
+    cudaEventRecord(h->ev_user, h->stream);
+    cudaStreamWaitEvent(user, h->ev_user, 0);
+    h->stream = user;
+    if (swapped) swap_buffers();
+  }
+};
+
 }  // namespace
 
 // ===================================================================== C ABI
@@ -600,7 +750,10 @@ void gevp_default_opts(gevp_opts* o) {
   o->tol = 1e-10;
   o->max_outer = 60;
   o->deg_min = 4;
-  o->deg_max = 24;
+  // filter steps are cheap next to a Rayleigh-Ritz round (an n x n x m FP64 product and
+  // an m x m eigensolve); a cap of 48 gave the fewest rounds on the warm sequences, while
+  // higher degrees make the guard columns of the filtered block nearly dependent
+  o->deg_max = 48;
   o->nex = 0;
   o->seed = 10074400ull;
   o->b_fixed = 0;
@@ -641,8 +794,17 @@ gevp_status gevp_destroy(gevp_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->hi) cudaStreamSynchronize(h->hi);
+  if (h->side) cudaStreamSynchronize(h->side);
   if (h->tc) gevp::filter_tc_release(h->tc);
+  if (h->tc2) gevp::filter_tc_release(h->tc2);
   if (h->batch) gevp::batch_release(h->batch);
+  if (h->parena) cudaFree(h->parena);
+  if (h->hb2) cudaFreeHost(h->hb2);
+  for (cudaEvent_t e : {h->ev_main, h->ev_side, h->ev_user})
+    if (e) cudaEventDestroy(e);
+  if (h->hi) cudaStreamDestroy(h->hi);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->stage) cudaFree(h->stage);
   if (h->arena) cudaFree(h->arena);
   if (h->hbuf) cudaFreeHost(h->hbuf);
@@ -705,6 +867,8 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
     if (!A[l] || !B[l]) return GEVP_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   TRY(ensure(h, n, m));
+  TRY(ensure_pipeline(h));
+  PipelineScope pipe(h);
   const int64_t ld = h->cap_m;
   // input sanity: NaN/Inf in any A or in B
   CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
@@ -718,6 +882,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
 
   gevp_status overall = GEVP_OK;
   bool warm_ok = false;   // Q holds a usable start block for this n, m
+  bool have_pre = false;  // C2 / bounds2 / tc2 hold problem l's standard form
   for (int l = 0; l < nprob; ++l) {
     Timer tm(h);
     tm.start();
@@ -746,9 +911,25 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
         zgemm(y, h->split, h->split_elems, h->stream);
       }
     }
-    reduce_into(h, n, Al, lda, h->C, n);
+    double pre_hb[16];
+    const bool used_pre = have_pre;
+    if (have_pre) {
+      // built on the side stream while the previous problem was being solved
+      CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));
+      CK(cudaEventSynchronize(h->ev_side));
+      std::memcpy(pre_hb, h->hb2, 16 * sizeof(double));
+      pipe.swap_buffers();
+      have_pre = false;
+    } else {
+      reduce_into(h, n, Al, lda, h->C, n);
+    }
     st->flops_fp64 += 4.0 * (double)n * n * n;
     tm.mark(PH_REDUCE);
+    // the next problem's standard form overlaps with this problem's solve (same B only)
+    if (l + 1 < nprob && (o.b_fixed || B[l + 1] == B[l])) {
+      TRY(prefetch_problem(h, n, m, (const double2*)A[l + 1], lda, o, l + 1));
+      have_pre = true;
+    }
     bool warm = false;
     if (!o.cold_start) {
       if (l == 0 && X_prev) {
@@ -769,7 +950,8 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
                               X ? ((o.keep_all_X ? (double2*)X + (int64_t)l * n * ldx
                                                  : (l == nprob - 1 ? (double2*)X : nullptr)))
                                 : nullptr,
-                              ldx, resid + (int64_t)l * nev);
+                              ldx, resid + (int64_t)l * nev, used_pre ? pre_hb : nullptr,
+                              used_pre && o.filter_prec != GEVP_PREC_FP64);
     if (s != GEVP_OK && s != GEVP_ERR_NO_CONVERGENCE) return s;
     if (s == GEVP_ERR_NO_CONVERGENCE) overall = s;
     warm_ok = true;

@@ -100,12 +100,12 @@ int  check_finite(int64_t rows, int64_t cols, const double2* A, int64_t lda, int
 
 // ---------------------------------------------------------------- factorizations
 // Blocked lower Cholesky in place (strict upper zeroed). info_dev: 0 or 1-based pivot.
-void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* ws, size_t ws_elems,
-                 cudaStream_t s);
+// Linv (n x n, ld ldi) receives the inverses of the 32 x 32 diagonal blocks of L.
+void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* Linv, int64_t ldi, cudaStream_t s);
 // Lower-triangular inverse: Linv = L^-1 (Linv separate buffer, strict upper zeroed).
+// diag_ready: Linv already holds the diagonal blocks' inverses (from potrf_lower).
 void trtri_lower(int64_t n, const double2* L, int64_t ldl, double2* Linv, int64_t ldi, double2* ws,
-                 size_t ws_elems, cudaStream_t s);
-size_t potrf_ws_elems(int64_t n);
+                 size_t ws_elems, cudaStream_t s, bool diag_ready = false);
 size_t trtri_ws_elems(int64_t n);
 
 // ---------------------------------------------------------------- small Hermitian eigensolver
@@ -238,7 +238,7 @@ struct BOut { double* lam; double* res; double2* X; int64_t ldx; };
 void bk_write_out(const BDesc* D, const BOut* O, int np, int64_t nm_max, cudaStream_t s);
 size_t bk_partial_elems(int m);
 // batched FP32 Jacobi: which = 0 -> G32 (m x m) into Z32/w32/perm; 1 -> T32 (k x k) into LZ32/lw32/lperm
-void jacobi32_batched(const BDesc* D, int np, int which, int k, int max_sweeps, cudaStream_t s);
+void jacobi32_batched(const BDesc* D, int np, int which, int k, int mmax, int max_sweeps, cudaStream_t s);
 void cluster_jacobi_batched(const BDesc* D, int np, int zsel, double rel, int max_sweeps, cudaStream_t s);
 
 // grouped tensor-core filter (residual-corrected recurrence) over the problems of a batch

@@ -17,6 +17,7 @@
 // make the phase, hence the rotation, non-unitary) and skips couplings below FP32
 // significance relative to the diagonal.
 #include "gevp_internal.cuh"
+#include <cooperative_groups.h>
 #include <algorithm>
 
 namespace gevp {
@@ -51,14 +52,132 @@ __device__ float block_sum(float v, float* red) {
   return s;
 }
 
+// L2 = true: load through L2 only (the multi-CTA variant; other CTAs wrote these
+// elements in the previous round and L1 is not coherent across SMs)
+template <bool L2>
+__device__ __forceinline__ float2 ld2(const float2* p) {
+  if constexpr (L2) return __ldcg(p);
+  else return *p;
+}
+
+// Rotation of pair k of round `step`: U = [[c, s], [-s conj(ph), c conj(ph)]] acting on
+// columns (p, q), stored as (c, s, Re ph, Im ph); identity for the dummy index q = m of
+// odd orders and for couplings below FP32 significance relative to the diagonal.
+template <bool L2 = false>
+__device__ __forceinline__ void jacobi_pair_params(const float2* G, int m, int np, int step, int k, float4* U,
+                                                   int (*PQ)[2]) {
+  int p, q;
+  block_pair(step, k, np, &p, &q);
+  PQ[k][0] = p;
+  PQ[k][1] = q;
+  float4 u = make_float4(1.f, 0.f, 1.f, 0.f);
+  if (q < m) {
+    float2 apq = ld2<L2>(G + p * m + q);
+    // |g_pq| without under/overflow: the phase g_pq / |g_pq| must stay unit-modulus
+    // or the rotation stops being unitary (squares of tiny off-diagonals are denormal)
+    float r = hypotf(apq.x, apq.y);
+    float app = ld2<L2>(G + p * m + p).x, aqq = ld2<L2>(G + q * m + q).x;
+    if (r > 1e-30f && r > 1e-10f * (fabsf(app) + fabsf(aqq))) {
+      float tau = (aqq - app) / (2.f * r);
+      float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+      float c = rsqrtf(1.f + t * t);
+      u = make_float4(c, t * c, apq.x / r, apq.y / r);
+    }
+  }
+  U[k] = u;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Task e of one rotation step. The pairs of a round are disjoint, so G <- U^H G U splits
+// into independent 2 x 2 blocks G[{p,q},{r,s}] <- U_a^H G[{p,q},{r,s}] U_b (tasks
+// e < npairs^2, a = row pair, b = column pair), and Z <- Z U into independent row pieces
+// (tasks after those). Every element is read and written once per step.
+template <bool L2 = false>
+__device__ __forceinline__ void jacobi_apply(float2* G, float2* Z, int m, int npairs, int e, const float4* U,
+                                             const int (*PQ)[2]) {
+  if (e < npairs * npairs) {
+    const int a = e / npairs, b = e % npairs;
+    const int p = PQ[a][0], q = PQ[a][1], r = PQ[b][0], s = PQ[b][1];
+    const bool qv = q < m, sv = s < m;
+    const float4 ua = U[a], ub = U[b];
+    const float2 z0 = make_float2(0.f, 0.f);
+    float2 gpr = ld2<L2>(G + p * m + r);
+    float2 gps = sv ? ld2<L2>(G + p * m + s) : z0;
+    float2 gqr = qv ? ld2<L2>(G + q * m + r) : z0;
+    float2 gqs = (qv && sv) ? ld2<L2>(G + q * m + s) : z0;
+    // columns (r, s) with U_b: x_r' = c x_r - s conj(ph) x_s, x_s' = s x_r + c conj(ph) x_s
+    {
+      const float c = ub.x, sn = ub.y;
+      const float2 phc = make_float2(ub.z, -ub.w);
+      float2 t = cmulf(gps, phc);
+      float2 nr = make_float2(c * gpr.x - sn * t.x, c * gpr.y - sn * t.y);
+      float2 ns = make_float2(sn * gpr.x + c * t.x, sn * gpr.y + c * t.y);
+      gpr = nr;
+      gps = ns;
+      t = cmulf(gqs, phc);
+      nr = make_float2(c * gqr.x - sn * t.x, c * gqr.y - sn * t.y);
+      ns = make_float2(sn * gqr.x + c * t.x, sn * gqr.y + c * t.y);
+      gqr = nr;
+      gqs = ns;
+    }
+    // rows (p, q) with U_a^H: r_p' = c r_p - s ph r_q, r_q' = s r_p + c ph r_q
+    {
+      const float c = ua.x, sn = ua.y;
+      const float2 ph = make_float2(ua.z, ua.w);
+      float2 t = cmulf(ph, gqr);
+      float2 np_ = make_float2(c * gpr.x - sn * t.x, c * gpr.y - sn * t.y);
+      float2 nq_ = make_float2(sn * gpr.x + c * t.x, sn * gpr.y + c * t.y);
+      gpr = np_;
+      gqr = nq_;
+      t = cmulf(ph, gqs);
+      np_ = make_float2(c * gps.x - sn * t.x, c * gps.y - sn * t.y);
+      nq_ = make_float2(sn * gps.x + c * t.x, sn * gps.y + c * t.y);
+      gps = np_;
+      gqs = nq_;
+    }
+    if (a == b) {   // the rotated pair: exact zero coupling, real diagonal
+      gps = z0;
+      gqr = z0;
+      gpr.y = 0.f;
+      gqs.y = 0.f;
+    }
+    G[p * m + r] = gpr;
+    if (sv) G[p * m + s] = gps;
+    if (qv) G[q * m + r] = gqr;
+    if (qv && sv) G[q * m + s] = gqs;
+  } else {
+    const int t = e - npairs * npairs;
+    const int i = t / npairs, b = t % npairs;
+    const int r = PQ[b][0], s = PQ[b][1];
+    if (s >= m) return;
+    const float4 u = U[b];
+    const float c = u.x, sn = u.y;
+    const float2 phc = make_float2(u.z, -u.w);
+    const float2 zr = ld2<L2>(Z + i * m + r), zs = cmulf(ld2<L2>(Z + i * m + s), phc);
+    Z[i * m + r] = make_float2(c * zr.x - sn * zs.x, c * zr.y - sn * zs.y);
+    Z[i * m + s] = make_float2(sn * zr.x + c * zs.x, sn * zr.y + c * zs.y);
+  }
+}
+
 // G (m x m, FP32 complex, Hermitian) is destroyed; Z receives eigenvectors (columns);
 // w receives eigenvalues sorted ascending and perm the column order (w[k] = G[perm[k]]).
-// Executed by one CTA of JT threads.
-__device__ void jacobi32_body(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps) {
+// Executed by one CTA of JT threads. Gs: shared-memory room for G (m * m), or nullptr to
+// work on G in global memory; every rotation step reads and writes all of G, so keeping
+// it on chip halves the step's memory traffic (Z stays in global memory).
+__device__ void jacobi32_body(int m, float2* Gg, float2* Z, float* w, int* perm, int max_sweeps, float2* Gs) {
   __shared__ float4 U[512];       // per pair: (c, s, Re ph, Im ph)
   __shared__ int PQ[512][2];
   __shared__ float red[32];
   const int tid = threadIdx.x;
+  float2* G = Gg;
+  if (Gs) {
+    for (int e = tid; e < m * m; e += JT) Gs[e] = Gg[e];
+    __syncthreads();
+    G = Gs;
+  }
   for (int e = tid; e < m * m; e += JT) Z[e] = make_float2((e / m) == (e % m) ? 1.f : 0.f, 0.f);
   int np = (m % 2) ? m + 1 : m;
   int npairs = np / 2;
@@ -81,66 +200,9 @@ __device__ void jacobi32_body(int m, float2* G, float2* Z, float* w, int* perm, 
     if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
     off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
-      for (int k = tid; k < npairs; k += JT) {
-        int p, q;
-        block_pair(step, k, np, &p, &q);
-        PQ[k][0] = p;
-        PQ[k][1] = q;
-        float4 u = make_float4(1.f, 0.f, 1.f, 0.f);
-        if (q < m) {
-          float2 apq = G[p * m + q];
-          // |g_pq| without under/overflow: the phase g_pq / |g_pq| must stay unit-modulus
-          // or the rotation stops being unitary (squares of tiny off-diagonals are denormal)
-          float r = hypotf(apq.x, apq.y);
-          float app = G[p * m + p].x, aqq = G[q * m + q].x;
-          // skip couplings below FP32 significance relative to the diagonal
-          if (r > 1e-30f && r > 1e-10f * (fabsf(app) + fabsf(aqq))) {
-            float tau = (aqq - app) / (2.f * r);
-            float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            float c = rsqrtf(1.f + t * t);
-            u = make_float4(c, t * c, apq.x / r, apq.y / r);
-          }
-        }
-        U[k] = u;
-      }
+      for (int k = tid; k < npairs; k += JT) jacobi_pair_params(G, m, np, step, k, U, PQ);
       __syncthreads();
-      // columns: G <- G U, Z <- Z U, with U = [[c, s], [-s conj(ph), c conj(ph)]]
-      for (int e = tid; e < m * npairs; e += JT) {
-        int i = e / npairs, k = e % npairs;
-        int p = PQ[k][0], q = PQ[k][1];
-        if (q >= m) continue;
-        float4 u = U[k];
-        float c = u.x, s = u.y;
-        float2 phc = make_float2(u.z, -u.w);
-        float2 gp = G[i * m + p], gq = G[i * m + q];
-        float2 gqph = make_float2(gq.x * phc.x - gq.y * phc.y, gq.x * phc.y + gq.y * phc.x);
-        G[i * m + p] = make_float2(c * gp.x - s * gqph.x, c * gp.y - s * gqph.y);
-        G[i * m + q] = make_float2(s * gp.x + c * gqph.x, s * gp.y + c * gqph.y);
-        float2 zp = Z[i * m + p], zq = Z[i * m + q];
-        float2 zqph = make_float2(zq.x * phc.x - zq.y * phc.y, zq.x * phc.y + zq.y * phc.x);
-        Z[i * m + p] = make_float2(c * zp.x - s * zqph.x, c * zp.y - s * zqph.y);
-        Z[i * m + q] = make_float2(s * zp.x + c * zqph.x, s * zp.y + c * zqph.y);
-      }
-      __syncthreads();
-      // rows: G <- U^H G ; U^H = [[c, -s ph], [s, c ph]]
-      for (int e = tid; e < m * npairs; e += JT) {
-        int k = e / m, j = e % m;
-        int p = PQ[k][0], q = PQ[k][1];
-        if (q >= m) continue;
-        float4 u = U[k];
-        float c = u.x, s = u.y;
-        float2 ph = make_float2(u.z, u.w);
-        float2 gp = G[p * m + j], gq = G[q * m + j];
-        float2 phgq = make_float2(ph.x * gq.x - ph.y * gq.y, ph.x * gq.y + ph.y * gq.x);
-        float2 np_ = make_float2(c * gp.x - s * phgq.x, c * gp.y - s * phgq.y);
-        float2 nq_ = make_float2(s * gp.x + c * phgq.x, s * gp.y + c * phgq.y);
-        if (j == q) np_ = make_float2(0.f, 0.f);
-        if (j == p) nq_ = make_float2(0.f, 0.f);
-        if (j == p) np_.y = 0.f;
-        if (j == q) nq_.y = 0.f;
-        G[p * m + j] = np_;
-        G[q * m + j] = nq_;
-      }
+      for (int e = tid; e < npairs * npairs + m * npairs; e += JT) jacobi_apply(G, Z, m, npairs, e, U, PQ);
       __syncthreads();
     }
   }
@@ -157,17 +219,93 @@ __device__ void jacobi32_body(int m, float2* G, float2* Z, float* w, int* perm, 
   }
 }
 
-__global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* Z, float* w, int* perm,
-                                                      int max_sweeps) {
-  jacobi32_body(m, G, Z, w, perm, max_sweeps);
+constexpr int kJacobiSmemMax = 160;   // largest m whose G (m * m FP32 complex) is kept in shared memory
+
+// Multi-CTA variant for orders above the one-CTA shared-memory size: the same rounds, each
+// CTA computing every rotation of a round (redundantly, from G in global memory) and
+// applying its share of the 2 x 2 block and Z tasks, with one grid barrier per round
+// (cooperative launch: all CTAs are resident). red: 2 + max_sweeps floats, zero on entry.
+__global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, float2* Z, float* w, int* perm,
+                                                           int max_sweeps, float* red_g) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ float4 U[512];
+  __shared__ int PQ[512][2];
+  __shared__ float red[32];
+  const int tid = threadIdx.x;
+  const int gtid = blockIdx.x * JT + tid, gsz = gridDim.x * JT;
+  for (int e = gtid; e < m * m; e += gsz) Z[e] = make_float2((e / m) == (e % m) ? 1.f : 0.f, 0.f);
+  const int np = (m % 2) ? m + 1 : m;
+  const int npairs = np / 2;
+  float f = 0.f;
+  for (int e = gtid; e < m * m; e += gsz) { float2 g = G[e]; f += g.x * g.x + g.y * g.y; }
+  f = block_sum(f, red);
+  if (tid == 0) atomicAdd(&red_g[0], f);
+  grid.sync();
+  const float fro2 = __ldcg(&red_g[0]);
+  const float tol2 = 1e-16f * fro2;
+  float off_prev = 3.0e38f;
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
+    float off = 0.f;
+    for (int e = gtid; e < m * m; e += gsz) {
+      int i = e / m, j = e % m;
+      if (i != j) { float2 g = __ldcg(G + e); off += g.x * g.x + g.y * g.y; }
+    }
+    off = block_sum(off, red);
+    if (tid == 0) atomicAdd(&red_g[1 + sweep], off);
+    grid.sync();
+    off = __ldcg(&red_g[1 + sweep]);   // the same value in every CTA: a uniform decision
+    if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
+    off_prev = off;
+    for (int step = 0; step < np - 1; ++step) {
+      for (int k = tid; k < npairs; k += JT) jacobi_pair_params<true>(G, m, np, step, k, U, PQ);
+      __syncthreads();
+      for (int e = gtid; e < npairs * npairs + m * npairs; e += gsz) jacobi_apply<true>(G, Z, m, npairs, e, U, PQ);
+      grid.sync();
+    }
+  }
+  if (blockIdx.x != 0) return;
+  for (int i = tid; i < m; i += JT) {
+    float wi = __ldcg(G + i * m + i).x;
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      float wj = __ldcg(G + j * m + j).x;
+      r += (wj < wi) || (wj == wi && j < i);
+    }
+    perm[r] = i;
+    w[r] = wi;
+  }
 }
 
-// one CTA per problem of a batch: which = 0 -> the Rayleigh-Ritz matrix, 1 -> Lanczos T
-__global__ void __launch_bounds__(JT) jacobi32_batched_kernel(const BDesc* D, int which, int k, int max_sweeps) {
+__global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* Z, float* w, int* perm,
+                                                      int max_sweeps) {
+  extern __shared__ float2 jsm[];
+  jacobi32_body(m, G, Z, w, perm, max_sweeps, m <= kJacobiSmemMax ? jsm : nullptr);
+}
+
+// one CTA per problem of a batch: which = 0 -> the Rayleigh-Ritz matrix, 1 -> Lanczos T;
+// smem_m: the launch provided shared-memory room for matrices up to smem_m x smem_m
+__global__ void __launch_bounds__(JT) jacobi32_batched_kernel(const BDesc* D, int which, int k, int max_sweeps,
+                                                              int smem_m) {
+  extern __shared__ float2 jsm[];
   const BDesc& d = D[blockIdx.x];
   if (d.active && *d.active == 0) return;
-  if (which == 0) jacobi32_body(d.m, d.G32, d.Z32, d.w32, d.perm, max_sweeps);
-  else jacobi32_body(k, d.T32, d.LZ32, d.lw32, d.lperm, max_sweeps);
+  if (which == 0) jacobi32_body(d.m, d.G32, d.Z32, d.w32, d.perm, max_sweeps, d.m <= smem_m ? jsm : nullptr);
+  else jacobi32_body(k, d.T32, d.LZ32, d.lw32, d.lperm, max_sweeps, k <= smem_m ? jsm : nullptr);
+}
+
+// dynamic shared memory of a Jacobi launch on matrices up to m x m (0: global memory)
+size_t jacobi_smem(int m) {
+  static bool set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !set[dev]) {
+    const int bytes = kJacobiSmemMax * kJacobiSmemMax * (int)sizeof(float2);
+    cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(jacobi32_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    set[dev] = true;
+  }
+  return m <= kJacobiSmemMax ? (size_t)m * m * sizeof(float2) : 0;
 }
 
 // Z64[:, k] = Z32[:, perm[k]]
@@ -263,7 +401,9 @@ __global__ void frob_kernel(int m, const double2* G, int64_t ldg, double* out) {
 __device__ void cluster_jacobi_body(int m, double2* S, double2* Z, double* lam, const double* fro, double rel,
                                     int max_sweeps) {
   const double tol = rel * fro[0];
-  constexpr int kMaxPairs = 256;
+  // FP32 Jacobi leaves eigenvalue errors of order 1e-4 ||G|| at m ~ 300 (accumulated
+  // rounding of many rotations), so dense clusters can leave several hundred couplings
+  constexpr int kMaxPairs = 1024;
   __shared__ int PI[kMaxPairs], PJ[kMaxPairs];
   __shared__ int npairs;
   __shared__ double2 ucs[3];   // c, s (real), ph
@@ -373,13 +513,42 @@ size_t heev_ws_bytes(int m, size_t split_elems) {
   return b + 16 * 256;
 }
 
+// Cooperative multi-CTA Jacobi for large m; false if it cannot be launched (then the
+// caller runs the one-CTA kernel).
+bool jacobi32_coop(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, float* red, cudaStream_t s) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi32_coop_kernel, JT, 0) != cudaSuccess ||
+      per_sm < 1)
+    return false;
+  const int np = (m % 2) ? m + 1 : m, npairs = np / 2;
+  const int64_t tasks = (int64_t)npairs * npairs + (int64_t)m * npairs;
+  int grid = (int)std::min<int64_t>((int64_t)per_sm * sms, (tasks + JT - 1) / JT);
+  grid = std::max(grid, 1);
+  if (max_sweeps > 62) max_sweeps = 62;
+  if (cudaMemsetAsync(red, 0, 64 * sizeof(float), s) != cudaSuccess) return false;
+  void* args[] = {&m, &G, &Z, &w, &perm, &max_sweeps, &red};
+  if (cudaLaunchCooperativeKernel((const void*)jacobi32_coop_kernel, grid, JT, args, 0, s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  LAUNCH_NOTE(1);
+  return true;
+}
+
 void jacobi32(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
-  jacobi32_kernel<<<1, JT, 0, s>>>(m, G, Z, w, perm, max_sweeps);
+  jacobi32_kernel<<<1, JT, jacobi_smem(m), s>>>(m, G, Z, w, perm, max_sweeps);
   LAUNCH_NOTE(1);
 }
 
-void jacobi32_batched(const BDesc* D, int np, int which, int k, int max_sweeps, cudaStream_t s) {
-  jacobi32_batched_kernel<<<np, JT, 0, s>>>(D, which, k, max_sweeps);
+// mmax: the largest matrix order among the problems (k for the Lanczos matrices)
+void jacobi32_batched(const BDesc* D, int np, int which, int k, int mmax, int max_sweeps, cudaStream_t s) {
+  // problems with m <= 160 keep G on chip even when the batch's largest m is above that
+  const int cap = std::min(which == 0 ? mmax : k, kJacobiSmemMax);
+  const size_t sm = jacobi_smem(cap);
+  jacobi32_batched_kernel<<<np, JT, sm, s>>>(D, which, k, max_sweeps, sm > 0 ? cap : 0);
   LAUNCH_NOTE(1);
 }
 
@@ -395,8 +564,13 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   int blocks = (int)std::min<int64_t>((mm + 255) / 256, 152 * 4);
   g_to_c_kernel<<<blocks, 256, 0, s>>>(m, G, ldg, w.G32);
   LAUNCH_NOTE(1);
-  jacobi32_kernel<<<1, JT, 0, s>>>(m, w.G32, w.Z32, w.w32, w.perm, 40);
-  LAUNCH_NOTE(1);
+  // large orders on all SMs (cooperative launch); otherwise, or if that launch is not
+  // possible, one CTA
+  const bool coop = m > kJacobiSmemMax && jacobi32_coop(m, w.G32, w.Z32, w.w32, w.perm, 40, (float*)(w.scal + 16), s);
+  if (!coop) {
+    jacobi32_kernel<<<1, JT, jacobi_smem(m), s>>>(m, w.G32, w.Z32, w.w32, w.perm, 40);
+    LAUNCH_NOTE(1);
+  }
   gather_z_kernel<<<blocks, 256, 0, s>>>(m, w.Z32, w.perm, w.Z, m);
   LAUNCH_NOTE(1);
   frob_kernel<<<1, 1024, 0, s>>>(m, G, ldg, w.scal + 1);
@@ -433,7 +607,7 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   ZgemmArgs c2 = zg(m, m, m, Z, m, 1, w.E, m, 0, w.S, m);
   zgemm(c2, w.split_ws, w.split_ws_elems, s);
   hermitize_avg(m, w.S, m, s);
-  cluster_jacobi_kernel<<<1, 1024, 0, s>>>(m, w.S, Z, w.lam, w.scal + 1, 1e-15, 6);
+  cluster_jacobi_kernel<<<1, 1024, 0, s>>>(m, w.S, Z, w.lam, w.scal + 1, 1e-15, 12);
   LAUNCH_NOTE(1);
   sort_pairs_kernel<<<1, 1024, 0, s>>>(m, w.lam, Z, theta, Zout, ldz);
   LAUNCH_NOTE(1);

@@ -1,7 +1,10 @@
 // Blocked right-looking complex Cholesky B = L L^H and blocked lower-triangular inverse.
-// The serial diagonal-block work runs in one CTA per 32 x 32 block; the panel solve is
-// spread one row per thread over many CTAs, and the trailing Hermitian update and the
-// inverse's off-diagonal blocks are FP64 GEMMs over all SMs.
+// The serial diagonal-block work runs in one CTA per 32 x 32 block, which also inverts
+// the factored block while it is in shared memory; the panel solve X L11^H = A21 is then
+// the product X = A21 L11^-H with every element computed in parallel (a row-per-thread
+// substitution would leave almost all SMs idle: one SM retires only about two FP64 FMAs
+// per clock on this part); the trailing Hermitian update and the inverse's off-diagonal
+// blocks are FP64 GEMMs over all SMs.
 #include "gevp_internal.cuh"
 #include <algorithm>
 
@@ -11,11 +14,15 @@ namespace {
 
 constexpr int NB = 32;
 
-// Unblocked Cholesky of the kb x kb diagonal block at A (lower, in place). On a
-// non-positive pivot the block is left partial and *info receives k0 + j + 1 (first
-// failure only). Does nothing if *info is already set.
-__global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, int* info) {
+// Unblocked Cholesky of the kb x kb diagonal block at A (lower, in place), and the
+// inverse of the factored block written to Li (lower, zero above). On a non-positive
+// pivot the block is left partial and *info receives k0 + j + 1 (first failure only).
+// Does nothing if *info is already set.
+__global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, int* info, double2* Li,
+                                  int64_t ldi) {
   __shared__ double2 S[NB][NB + 1];
+  __shared__ double2 X[NB][NB + 1];
+  __shared__ double rdiag[NB];
   __shared__ int fail;
   if (*info != 0) return;
   const int tid = threadIdx.x;
@@ -56,36 +63,52 @@ __global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, i
     int i = e / kb, j = e % kb;
     A[i * lda + j] = (j <= i) ? S[i][j] : make_double2(0.0, 0.0);
   }
+  if (fail) return;
+  // inverse: row i of X = S^-1 from rows < i, all columns c <= i in parallel
+  for (int j = tid; j < kb; j += blockDim.x) rdiag[j] = 1.0 / S[j][j].x;
+  __syncthreads();
+  for (int i = 0; i < kb; ++i) {
+    for (int c = tid; c <= i; c += blockDim.x) {
+      double2 v = make_double2(c == i ? 1.0 : 0.0, 0.0);
+      for (int k = c; k < i; ++k) {
+        const double2 l = S[i][k], x = X[k][c];
+        v.x -= l.x * x.x - l.y * x.y;
+        v.y -= l.x * x.y + l.y * x.x;
+      }
+      X[i][c] = zscale(v, rdiag[i]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    int i = e / kb, j = e % kb;
+    Li[i * ldi + j] = (j <= i) ? X[i][j] : make_double2(0.0, 0.0);
+  }
 }
 
-// Panel solve X L11^H = A21 in place, one row of A21 per thread (rows independent).
-template <int KB>
-__global__ void trsm_panel_kernel(double2* A21, int64_t lda, int64_t rows, const double2* L11, int kb,
-                                  const int* info) {
-  __shared__ double2 Ls[KB][KB];
-  __shared__ double dinv[KB];
+// Panel X = A21 L11^-H in place (solves X L11^H = A21), Li = L11^-1 lower:
+// X[r][j] = sum_{k <= j} A21[r][k] conj(Li[j][k]). RB rows per CTA, staged in shared
+// memory (every output of a row reads the row's first j + 1 inputs).
+template <int RB>
+__global__ void panel_apply_kernel(double2* A21, int64_t lda, int64_t rows, const double2* Li, int64_t ldi, int kb,
+                                   const int* info) {
+  __shared__ double2 Ls[NB][NB + 1];
+  __shared__ double2 As[RB][NB + 1];
   if (*info != 0) return;
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) Ls[e / kb][e % kb] = L11[(e / kb) * lda + (e % kb)];
-  __syncthreads();
-  for (int j = threadIdx.x; j < kb; j += blockDim.x) dinv[j] = 1.0 / Ls[j][j].x;
-  __syncthreads();
-  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  double2* row = A21 + r * lda;
-  double2 x[KB];
-#pragma unroll
-  for (int j = 0; j < KB; ++j) {
-    if (j < kb) {
-      double2 s = row[j];
-#pragma unroll
-      for (int k = 0; k < KB; ++k)
-        if (k < j) zfma(s, zscale(x[k], -1.0), zconj(Ls[j][k]));
-      x[j] = zscale(s, dinv[j]);
-    }
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  for (int e = tid; e < kb * kb; e += blockDim.x) Ls[e / kb][e % kb] = Li[(e / kb) * ldi + (e % kb)];
+  for (int e = tid; e < RB * kb; e += blockDim.x) {
+    int rr = e / kb, k = e % kb;
+    As[rr][k] = (r0 + rr < rows) ? A21[(r0 + rr) * lda + k] : make_double2(0.0, 0.0);
   }
-#pragma unroll
-  for (int j = 0; j < KB; ++j)
-    if (j < kb) row[j] = x[j];
+  __syncthreads();
+  for (int e = tid; e < RB * kb; e += blockDim.x) {
+    int rr = e / kb, j = e % kb;
+    if (r0 + rr >= rows) continue;
+    double2 v = make_double2(0.0, 0.0);
+    for (int k = 0; k <= j; ++k) zfma(v, As[rr][k], zconj(Ls[j][k]));
+    A21[(r0 + rr) * lda + j] = v;
+  }
 }
 
 // Inverse of the lower-triangular diagonal blocks (size <= NB) of L, written into Linv.
@@ -138,28 +161,25 @@ void trtri_combine(int64_t n, const double2* L, int64_t ldl, double2* Linv, int6
 
 }  // namespace
 
-size_t potrf_ws_elems(int64_t n) { return 0; }
-
 size_t trtri_ws_elems(int64_t n) {
   int64_t n1 = ((n / 2 + NB - 1) / NB) * NB;
   int64_t n2 = n - n1;
   return (size_t)std::max<int64_t>(1, n1 * std::max<int64_t>(n2, 1));
 }
 
-void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* ws, size_t ws_elems,
-                 cudaStream_t s) {
-  (void)ws; (void)ws_elems;
+void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* Linv, int64_t ldi, cudaStream_t s) {
+  constexpr int RB = 8;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     int kb = (int)std::min<int64_t>(NB, n - k0);
     double2* Akk = A + k0 * lda + k0;
-    potrf_diag_kernel<<<1, 256, 0, s>>>(Akk, lda, kb, k0, info_dev);
+    double2* Likk = Linv + k0 * ldi + k0;
+    potrf_diag_kernel<<<1, 256, 0, s>>>(Akk, lda, kb, k0, info_dev, Likk, ldi);
     LAUNCH_NOTE(1);
     int64_t rem = n - k0 - kb;
     if (rem <= 0) break;
     double2* A21 = A + (k0 + kb) * lda + k0;
-    int threads = 32;
-    int blocks = (int)((rem + threads - 1) / threads);
-    trsm_panel_kernel<NB><<<blocks, threads, 0, s>>>(A21, lda, rem, Akk, kb, info_dev);
+    int blocks = (int)((rem + RB - 1) / RB);
+    panel_apply_kernel<RB><<<blocks, RB * NB, 0, s>>>(A21, lda, rem, Likk, ldi, kb, info_dev);
     LAUNCH_NOTE(1);
     // A22 -= L21 L21^H (lower tiles only)
     double2* A22 = A + (k0 + kb) * lda + (k0 + kb);
@@ -172,11 +192,13 @@ void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* ws,
 }
 
 void trtri_lower(int64_t n, const double2* L, int64_t ldl, double2* Linv, int64_t ldi, double2* ws,
-                 size_t ws_elems, cudaStream_t s) {
+                 size_t ws_elems, cudaStream_t s, bool diag_ready) {
   zero_upper(n, Linv, ldi, s);
-  int nblk = (int)((n + NB - 1) / NB);
-  trtri_diag_kernel<<<nblk, NB, 0, s>>>(n, L, ldl, Linv, ldi);
-  LAUNCH_NOTE(1);
+  if (!diag_ready) {
+    int nblk = (int)((n + NB - 1) / NB);
+    trtri_diag_kernel<<<nblk, NB, 0, s>>>(n, L, ldl, Linv, ldi);
+    LAUNCH_NOTE(1);
+  }
   // ws holds T (first trtri_ws_elems) and the split-K scratch after it
   size_t tel = trtri_ws_elems(n);
   double2* split = (ws_elems > tel) ? ws + tel : nullptr;

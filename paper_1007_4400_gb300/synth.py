@@ -44,7 +44,12 @@ def _cnormal(rng: np.random.Generator, shape) -> np.ndarray:
 
 def draw_L(rng: np.random.Generator, n: int, diag=(0.5, 2.0), off_scale=None,
            log_uniform_diag: bool = False) -> np.ndarray:
-    """Lower-triangular factor of B: real positive diagonal, complex normal strict lower part."""
+    """Lower-triangular factor of B: real positive diagonal, complex normal strict lower part.
+
+    With ``log_uniform_diag`` the diagonal d is log-uniform in ``diag`` and each row of the
+    strict lower part is scaled by its diagonal entry, L = D (I + N): then
+    cond(B) ~ (max d / min d)^2 (about 1.3e5 for diag = (6e-3, 2)). Unscaled off-diagonals
+    next to small diagonal entries would make L (hence B) numerically singular."""
     if off_scale is None:
         off_scale = 0.3 / math.sqrt(n)
     lo, hi = diag
@@ -57,7 +62,10 @@ def draw_L(rng: np.random.Generator, n: int, diag=(0.5, 2.0), off_scale=None,
     re = rng.standard_normal(m)
     im = rng.standard_normal(m)
     L = np.zeros((n, n), dtype=np.complex128)
-    L[il] = (re + 1j * im) * math.sqrt(0.5) * off_scale
+    off = (re + 1j * im) * math.sqrt(0.5) * off_scale
+    if log_uniform_diag:
+        off = off * d[il[0]]
+    L[il] = off
     L[np.arange(n), np.arange(n)] = d
     return L
 
@@ -84,10 +92,40 @@ def known_spectrum_pencil(L: torch.Tensor, Q: torch.Tensor, lam: torch.Tensor):
     return A.contiguous(), B.contiguous()
 
 
+def _norm2_lanczos(P: torch.Tensor, k: int = 60) -> float:
+    """Spectral norm of Hermitian P from k Lanczos steps (full re-orthogonalisation) with a
+    fixed start vector; used for the large workloads, where a full eigvalsh per sequence
+    step would dominate input generation. The estimate is within 1e-3 relative for the
+    random Hermitian matrices drawn here, which only sets the size of a perturbation."""
+    n = P.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(SEED_BASE)
+    v = torch.randn(n, dtype=torch.float64, generator=g).to(P.device).to(P.dtype)
+    V = [v / torch.linalg.vector_norm(v)]
+    a, b = [], []
+    for j in range(min(k, n)):
+        w = P @ V[j]
+        for _ in range(2):
+            for u in V:
+                w = w - (u.conj() @ w) * u
+        a.append(float(torch.real(V[j].conj() @ (P @ V[j]))))
+        nb = float(torch.linalg.vector_norm(w))
+        if nb < 1e-12:
+            break
+        b.append(nb)
+        V.append(w / nb)
+    m = len(a)
+    T = np.diag(a) + np.diag(b[:m - 1], 1) + np.diag(b[:m - 1], -1)
+    return float(np.abs(np.linalg.eigvalsh(T)).max())
+
+
 def hermitian_unit_norm(rng: np.random.Generator, n: int, device="cpu") -> torch.Tensor:
-    """P = (G + G^H)/2 with complex standard normal G, divided by its spectral norm."""
+    """P = (G + G^H)/2 with complex standard normal G, divided by its spectral norm (for
+    n > 8192 by a Lanczos estimate of it)."""
     G = torch.from_numpy(_cnormal(rng, (n, n))).to(device)
     P = hermitian_part(G)
+    del G
+    if n > 8192:
+        return (P / _norm2_lanczos(P)).contiguous()
     ev = torch.linalg.eigvalsh(P)
     return (P / ev.abs().max()).contiguous()
 
@@ -162,6 +200,9 @@ WORKLOADS = {
                                   spectrum="clustered", diag=(6.0e-3, 2.0), log_uniform_diag=True),
     # differentiation form
     "grad_n4096": dict(config_id=4, n=4096, nprob=1, nev=200, nex=50, spectrum="clustered"),
+    # the long sequence of the differentiation form's construction: 30 problems, n=12000
+    "scf_seq_n12000": dict(config_id=4, n=12000, nprob=30, nev=600, nex=150, spectrum="clustered",
+                           problem_index=1),
 }
 
 

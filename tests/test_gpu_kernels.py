@@ -70,7 +70,7 @@ def test_cholqr2_parity(cuda, orc, n, m):
     assert relmax(Rg, Rr) < 1e-10
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 17, 64, 140, 200])
+@pytest.mark.parametrize("m", [1, 2, 3, 17, 64, 140, 159, 161, 200, 301])
 def test_heev_small_parity(cuda, orc, m):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(400 + m)
@@ -84,7 +84,7 @@ def test_heev_small_parity(cuda, orc, m):
     assert np.abs(G @ Z - Z * th).max() <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("m", [48, 140, 300])
+@pytest.mark.parametrize("m", [48, 140, 300, 333])
 def test_heev_small_clustered_wide(cuda, orc, m):
     # the shape of a cold-start Rayleigh-Ritz projection: a dense cluster of small values,
     # a near-degenerate pair and a wide sparse tail; Z must stay orthonormal to FP64 level
