@@ -137,3 +137,22 @@ def deviation_angles(X_old, X_new, B):
     nn = np.sqrt(np.abs(np.sum(np.conj(X_new) * BXn, axis=0)))
     c = np.clip(num / (no * nn), 0.0, 1.0)
     return np.arccos(c) / (math.pi / 2)
+
+
+def matrix_variation(A_new, A_old, thresholds):
+    """The paper's entry-variation statistics between consecutive Hamiltonians (Sec.
+    "Matrix generation"): delta = the largest entry variation max_ij |A_new - A_old|_ij,
+    and for each threshold fraction p the number of entries whose variation exceeds
+    p * delta. Compared as squares in FP64 with the operations in this order and no fused
+    multiply-add: d2 = dr*dr + di*di, delta2 = max d2, an entry counts for p when
+    d2 > (p*p) * delta2. Returns (delta, counts, mask for thresholds[0])."""
+    D = np.asarray(A_new, dtype=np.complex128) - np.asarray(A_old, dtype=np.complex128)
+    dr, di = D.real, D.imag
+    d2 = dr * dr + di * di
+    delta2 = float(d2.max()) if d2.size else 0.0
+    counts = []
+    for p in thresholds:
+        thr2 = (float(p) * float(p)) * delta2
+        counts.append(int(np.count_nonzero(d2 > thr2)))
+    mask = (d2 > (float(thresholds[0]) * float(thresholds[0])) * delta2) if len(thresholds) else None
+    return math.sqrt(delta2), counts, mask

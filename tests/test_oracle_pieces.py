@@ -87,3 +87,43 @@ def test_principal_sines_B_inner_product(orc):
     X = crandn(rng, n, 3)
     s = pieces.principal_sines(X, X @ crandn(rng, 3, 3), B)
     assert s.max() < 1e-7
+
+
+def test_matrix_variation_hand_case():
+    """delta and the counts on a difference whose entries are known exactly: moduli
+    5 (3+4i), 1 (exactly at p = 0.2 of delta), 0.5 (exactly at p = 0.1), 0.25 (at p = 0.05):
+    entries exactly at a threshold are not above it (the comparison is strict);
+    0.25j, 0 elsewhere."""
+    from oracle import pieces
+    A_old = np.zeros((4, 4), dtype=np.complex128)
+    A_new = A_old.copy()
+    A_new[0, 1], A_new[1, 0] = 3 + 4j, 3 - 4j
+    A_new[2, 2] = 1.0
+    A_new[3, 0], A_new[0, 3] = 0.5, 0.5
+    A_new[1, 3], A_new[3, 1] = 0.25j, -0.25j
+    A_old[2, 3] = A_new[2, 3] = 7.0 - 2.0j          # unchanged entry, nonzero
+    delta, counts, mask = pieces.matrix_variation(A_new, A_old, [0.1, 0.0, 0.05, 0.2, 1.0])
+    assert delta == 5.0
+    assert counts == [3, 7, 5, 2, 0]   # p = 0.2: threshold 1.0, the diagonal 1 is not above it
+    assert mask.sum() == 3 and mask[0, 1] and mask[1, 0] and mask[2, 2]
+
+
+def test_matrix_variation_invariants():
+    """Counts fall as the threshold rises, count(0) is the number of changed entries, the
+    largest entry defines delta (count at p = 1 is zero), and a Hermitian difference gives
+    counts of the same parity as its changed diagonal entries."""
+    from oracle import pieces
+    rng = np.random.default_rng(5)
+    n = 37
+    A = crandn(rng, n, n)
+    A = A + A.conj().T
+    P = crandn(rng, n, n) * (rng.random((n, n)) < 0.2)
+    P = P + P.conj().T
+    ps = [0.0, 0.01, 0.1, 0.3, 0.7, 1.0]
+    delta, counts, _ = pieces.matrix_variation(A + 1e-3 * P, A, ps)
+    assert all(a >= b for a, b in zip(counts, counts[1:]))
+    changed = np.count_nonzero((A + 1e-3 * P) != A)
+    assert counts[0] == changed and counts[-1] == 0
+    diag_changed = np.count_nonzero(np.diag(A + 1e-3 * P) != np.diag(A))
+    assert (counts[0] - diag_changed) % 2 == 0
+    assert abs(delta - np.abs((A + 1e-3 * P) - A).max()) <= 1e-15 * delta
