@@ -46,7 +46,9 @@ def parse():
                    help="where the synthetic inputs are generated (cpu for runs under ncu)")
     p.add_argument("--kpoints", type=int, default=64, help="kpoint_batch workload: number of k-points")
     p.add_argument("--seq-steps", type=int, default=10, help="kpoint_batch workload: problems per k-point")
-    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched"], default=None,
+    p.add_argument("--reduce-slices", type=int, default=0,
+                   help="digits of the emulated FP64 products of the reduction (0: FP64 pipe)")
+    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki"], default=None,
                    help="run only a few launches of one kernel (n 2048, m 140) for ncu captures")
     return p.parse_args()
 
@@ -56,6 +58,65 @@ def kernel_case(args):
     import torch
     from paper_1007_4400_gb300 import gevp, synth
     dev = torch.device("cuda", 0)
+    if args.kernel_case == "variation":
+        # entry-variation statistics of two n = 6144 matrices (1.2 GB, beyond L2), timed with
+        # CUDA events. Algorithmic bytes: both matrices read once (32 n^2); the kernels also
+        # write and re-read the squared moduli (16 n^2) and spend 5 FP64 operations per entry
+        n = 6144
+        g = torch.Generator(device=dev).manual_seed(11)
+        A0 = torch.randn((n, n), dtype=torch.complex128, device=dev, generator=g)
+        A1 = A0 + 1e-3 * torch.randn((n, n), dtype=torch.complex128, device=dev, generator=g)
+        ps = [0.01, 0.1, 0.5]
+        for _ in range(3):
+            gevp.matrix_variation(A1, A0, ps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            d, c, _ = gevp.matrix_variation(A1, A0, ps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        alg = 32.0 * n * n
+        print(json.dumps({"kernel_case": "variation", "n": n, "ms": ms, "alg_bytes": alg,
+                          "GBps": alg / (ms * 1e-3) / 1e9, "bytes_moved": 48.0 * n * n,
+                          "fp64_ops": 5.0 * n * n, "delta": d, "counts": c}))
+        return 0
+    if args.kernel_case == "ozaki":
+        # the emulated FP64 product D = A B^H (n = 2048, 8 digits) and the reduction to
+        # standard form with and without it, timed with CUDA events (inputs are 67 MB per
+        # matrix; the digit planes, 200+ MB per operand, exceed L2)
+        n = 2048
+        g = torch.Generator(device=dev).manual_seed(13)
+        A = torch.randn((n, n), dtype=torch.complex128, device=dev, generator=g)
+        Bm = torch.randn((n, n), dtype=torch.complex128, device=dev, generator=g)
+        H = 0.5 * (A + A.conj().T)
+        P = torch.eye(n, dtype=torch.complex128, device=dev) * 2.0 + 0.01 * H
+        def timed(f, reps=5):
+            for _ in range(2):
+                f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                out = f()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps, out
+        ms_oz, D = timed(lambda: gevp.zgemm_emulated(A, Bm, 8))
+        ref = A @ Bm.conj().T
+        err = float((D - ref).abs().max() / ref.abs().max())
+        ms_red64, (L0, C0) = timed(lambda: gevp.reduce(H, P))
+        ms_red_oz, (L1, C1) = timed(lambda: gevp.reduce(H, P, slices=8))
+        cdiff = float((C1 - C0).abs().max() / C0.abs().max())
+        pairs = 36
+        print(json.dumps({"kernel_case": "ozaki", "n": n, "ms_zgemm_emulated": ms_oz,
+                          "fp64_equiv_tflops": 8.0 * n ** 3 / (ms_oz * 1e-3) / 1e12,
+                          "bf16_exec_tflops": pairs * 8.0 * n ** 3 / (ms_oz * 1e-3) / 1e12,
+                          "max_err_vs_cublas_zgemm": err, "ms_reduce_fp64": ms_red64, "ms_reduce_emulated": ms_red_oz,
+                          "reduce_rel_diff": cdiff}))
+        return 0
     if args.kernel_case == "batched":
         # one step of a small k-point batch (inputs built on the host), FP32-class filter:
         # the grouped tcgen05 filter, grouped FP64 GEMMs and the batched small kernels
@@ -353,7 +414,7 @@ def main():
         seq.B = seq.B.to(dev)
     nprob, n, nev, nex = len(seq.A), seq.n, seq.nev, seq.nex
     m = nev + nex
-    opts = dict(nex=nex, filter_prec=args.prec)
+    opts = dict(nex=nex, filter_prec=args.prec, reduce_slices=args.reduce_slices)
     peaks = gevp.probe_peaks(local)
 
     def step(**kw):

@@ -73,6 +73,14 @@ typedef struct {
   int lanczos_steps;    /* steps of the Lanczos bound estimator                         */
   int refine_iters;     /* refinement steps of the small eigensolver (>= 1)             */
   int keep_all_X;       /* 1: X receives every problem's eigenvectors (nprob*n*nev)     */
+  int refresh_window;   /* 0: off. k > 0: after k consecutive warm-started problems that */
+                        /* needed at least as many filter matvecs as the latest cold one, */
+                        /* the next problem starts cold (the paper's refresh when progress */
+                        /* flattens out, Sec. "A new computational philosophy")           */
+  int reduce_slices;    /* 0: the n^3 products of the reduction to standard form run on the */
+                        /* FP64 pipe. 1..8: they are emulated on the tensor cores with that */
+                        /* many 7-bit digits per entry (Ozaki scheme, exact digit products; */
+                        /* 8 digits keep FP64-class accuracy), see gevp_zgemm_emulated      */
 } gevp_opts;
 
 /* Per-problem counters and CUDA-event phase times (milliseconds). */
@@ -88,6 +96,7 @@ typedef struct {
   double flops_lowp;    /* executed-flop model, tensor-core filter work (complex, 8/MAC) */
   double max_resid;
   double orth_err;      /* max |Q^H Q - I| of the returned block (B-orthonormality of X)  */
+  int cold;             /* 1 if this problem started from a random block                 */
   float ms_chol, ms_reduce, ms_bounds, ms_filter, ms_orth, ms_rr, ms_resid, ms_final, ms_total;
 } gevp_stats;
 
@@ -235,6 +244,83 @@ gevp_status gevp_spectral_bounds(gevp_handle h, int64_t n, const void* C, int64_
  * X n x nev B-orthonormal eigenvectors (ld ldx), Lambda device (nev); GA, GB n x n (ld ldg). */
 gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* X, int64_t ldx,
                                  const double* Lambda, double gE, void* GA, void* GB, int64_t ldg);
+
+/* Entry-variation statistics between the Hamiltonians of consecutive self-consistent
+ * iterations (Sec. "Matrix generation": the largest entry variation delta_{n+1} and the
+ * entries of (A_{n+1} - A_n) / delta_{n+1} above a threshold fraction p_t, whose share
+ * tells how much of the matrix would have to be regenerated).
+ *   A_new, A_old: n x n device (ld lda, ldb). p_t: host array of nthr (<= 16) fractions.
+ *   Outputs (host): *delta = max_ij |A_new - A_old|_ij; counts[k] = number of entries with
+ *   |A_new - A_old|_ij > p_t[k] * delta. The comparison is made on squares in FP64,
+ *   d2 = dr*dr + di*di (each product and the sum rounded separately) against
+ *   (p*p) * delta^2, so the counts are exact for that arithmetic.
+ *   mask: nullable device n x n bytes (row-major, ld n): 1 where the entry is above
+ *   p_t[0] * delta, else 0.
+ *   The handle keeps an n x n scratch of 8-byte words (the squared moduli), grown on
+ *   demand. GEVP_ERR_INVALID_VALUE if a difference is NaN. Returns after the work is
+ *   complete. */
+gevp_status gevp_matrix_variation(gevp_handle h, int64_t n, const void* A_new, int64_t lda, const void* A_old,
+                                  int64_t ldb, int nthr, const double* p_t, double* delta, int64_t* counts,
+                                  void* mask);
+
+/* Deviation angles between the eigenvectors of consecutive problems, and the re-indexing
+ * that matches them (Sec. "A new computational philosophy", paragraph "Eigenvectors
+ * evolution": eigenvalue order is not a reliable index from one iteration to the next, so
+ * each old eigenvector is compared with the new one at the smallest angle; angles are
+ * normalised so that 1.00 = pi/2).
+ *   X_old: n x k_old, X_new: n x k_new (k_old <= k_new), device, row-major complex128
+ *   (ld ldo, ldn), columns the eigenvectors. B: device n x n HPD (ld ldb), or NULL for the
+ *   Euclidean inner product.
+ *   c_ij = |x_old_i^H B x_new_j| / (||x_old_i||_B ||x_new_j||_B), clamped to [0, 1].
+ *   cosines: nullable device k_old x k_new doubles (row-major, ld ldc) receiving c.
+ *   perm: nullable host int64[k_old]. Given, it receives the re-indexing: the assignment of
+ *   each old vector to a distinct new one minimising sum_i (1 - c_{i,perm[i]}), where a pair
+ *   with |lam_old[i] - lam_new[j]| > window costs more than any assignment of pairs inside
+ *   the window (so the fewest pairs possible lie outside it). The paper gives no algorithm;
+ *   this is an optimal assignment (Hungarian method on the host, exact for the cosines in
+ *   FP64; when several assignments tie, any one of them). NULL: no re-indexing, column i is
+ *   matched with column i.
+ *   lam_old, lam_new: host eigenvalues (k_old, k_new); required when window is finite,
+ *   ignored when window = +INFINITY (no window). window >= 0.
+ *   Outputs (host, each nullable): theta[i] = acos(c_{i,match(i)}) / (pi/2); *cost = sum of
+ *   1 - c over matched pairs inside the window; *n_outside = matched pairs outside it.
+ *   GEVP_ERR_INVALID_VALUE if a B-norm is zero or not finite. Device scratch of about
+ *   16 n (k_old + k_new) + 24 k_old k_new bytes is kept by the handle (grown on demand).
+ *   Returns after the work is complete. */
+gevp_status gevp_deviation_angles(gevp_handle h, int64_t n, int k_old, int k_new, const void* X_old, int64_t ldo,
+                                  const void* X_new, int64_t ldn, const void* B, int64_t ldb, const double* lam_old,
+                                  const double* lam_new, double window, double* cosines, int64_t ldc, int64_t* perm,
+                                  double* theta, double* cost, int64_t* n_outside);
+
+/* The host step of the re-indexing above, on its own (no device, no handle): the
+ * assignment of each of the ko rows of a ko x kn cost table (host, row-major, ld kn,
+ * ko <= kn, finite entries) to a distinct column minimising the summed cost; perm (host,
+ * ko) receives the column of each row. Hungarian method, shortest-augmenting-path form.
+ * GEVP_ERR_INVALID_ARG on bad sizes, null pointers or a cost that is not finite. */
+gevp_status gevp_assign_min_cost(int ko, int kn, const double* cost, int64_t* perm);
+
+/* FP64 complex product emulated on the tensor cores (Ozaki scheme; beyond the paper, which
+ * keeps every step in FP64): D (M x N) = A B^H with A M x K and B N x K, device row-major
+ * complex128 (ld lda, ldb, ldd). Each row of A and of B is scaled by a power of two so its
+ * largest real or imaginary part lies in [1/4, 1/2), rounded to `slices` signed 7-bit
+ * digits (1..8) and the digit planes are multiplied exactly in BF16 with FP32
+ * accumulation (units of at most 2048 complex terms); pairs of digits whose weights sum
+ * past the last digit are left out; the exact integer sums are combined in FP64.
+ *   Error of entry (i, j): at most about 2K (slices + 3) 2^(-7 slices + 2) max_k|A_ik|
+ *   max_k|B_jk| (FP64's own bound is K u sum_k |A_ik||B_jk|, u = 2^-53); with 8 digits
+ *   the two are of the same order.
+ *   K <= 30720 (else GEVP_ERR_UNSUPPORTED); GEVP_ERR_INVALID_VALUE on NaN or Inf in A or B.
+ *   Device scratch of slices * (4 M_pad + 6 N_pad) * K_pad bytes (M_pad, N_pad: M, N
+ *   rounded up to 128; K_pad: K rounded up to 64) is kept by the handle. Needs an sm_103 device (GEVP_ERR_UNSUPPORTED otherwise).
+ *   Returns after the work is complete. */
+gevp_status gevp_zgemm_emulated(gevp_handle h, int M, int N, int K, const void* A, int64_t lda, const void* B,
+                                int64_t ldb, void* D, int64_t ldd, int slices);
+
+/* gevp_reduce with the two n^3 products of the reduction (T = L^-1 tril(A) with the
+ * diagonal halved, M = T L^-H, C = M + M^H) emulated as in gevp_zgemm_emulated with
+ * `slices` digits. n <= 30720. The same outputs and errors as gevp_reduce. */
+gevp_status gevp_reduce_emulated(gevp_handle h, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                 void* L, int64_t ldl, void* C, int64_t ldc, int64_t* info, int slices);
 
 /* Measured FP64 FMA, FP64 DMMA and FP32 FMA rates of this device in TFLOP/s (host out[3]). */
 gevp_status gevp_probe_peaks(gevp_handle h, double* out);

@@ -156,3 +156,37 @@ def matrix_variation(A_new, A_old, thresholds):
         counts.append(int(np.count_nonzero(d2 > thr2)))
     mask = (d2 > (float(thresholds[0]) * float(thresholds[0])) * delta2) if len(thresholds) else None
     return math.sqrt(delta2), counts, mask
+
+
+def overlap_cosines(X_old, X_new, B):
+    """c_ij = |x_old_i^H B x_new_j| / (||x_old_i||_B ||x_new_j||_B): the cosines of the
+    angles between every old and every new eigenvector in the B inner product."""
+    B = np.asarray(B)
+    X_old = np.asarray(X_old)
+    X_new = np.asarray(X_new)
+    O = X_old.conj().T @ (B @ X_new)
+    no = np.sqrt(np.abs(np.sum(np.conj(X_old) * (B @ X_old), axis=0)))
+    nn = np.sqrt(np.abs(np.sum(np.conj(X_new) * (B @ X_new), axis=0)))
+    return np.clip(np.abs(O) / np.outer(no, nn), 0.0, 1.0)
+
+
+def reindex(X_old, X_new, B, lam_old, lam_new, window=np.inf):
+    """Re-indexing of the new eigenvectors against the old (Sec. "A new computational
+    philosophy", paragraph "Eigenvectors evolution": each eigenvector is compared with the
+    one at the next iteration that it deviates least from; the paper names the criterion,
+    angle minimisation, but gives no algorithm). Reading: the assignment perm of every old
+    vector to a distinct new one minimising sum_i (1 - c_{i, perm[i]}), where a pair whose
+    eigenvalues differ by more than `window` costs k_old + 1, more than any assignment of
+    pairs inside the window. Solved with scipy's linear_sum_assignment (a library
+    primitive). Returns (perm, cost of the pairs inside the window, pairs outside it)."""
+    from scipy.optimize import linear_sum_assignment
+    c = overlap_cosines(X_old, X_new, B)
+    ko = c.shape[0]
+    far = np.abs(np.asarray(lam_old)[:, None] - np.asarray(lam_new)[None, :]) > window
+    cost = np.where(far, ko + 1.0, 1.0 - c)
+    r, col = linear_sum_assignment(cost)
+    perm = np.empty(len(r), dtype=np.int64)
+    perm[r] = col
+    out = far[np.arange(ko), perm]
+    inside = float((1.0 - c[np.arange(ko), perm])[~out].sum())
+    return perm, inside, int(out.sum())

@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(256) b_cheb_coef(const BDesc* D, int deg_min, 
     return;
   }
   const int m = d.m, nev = d.nev;
-  const int cap = max(deg_min, min(min(deg_cap[blockIdx.x], d.flags[13]), kBDegMax));
+  const int cap0 = max(deg_min, min(min(deg_cap[blockIdx.x], d.flags[13]), kBDegMax));
   if (threadIdx.x == 0) {
     double hi = d.bounds[2];
     double lo = d.theta[m - 1];
@@ -690,13 +690,22 @@ __global__ void __launch_bounds__(256) b_cheb_coef(const BDesc* D, int deg_min, 
   }
   __syncthreads();
   const double e = 0.5 * (s_hi - s_lo), c = 0.5 * (s_hi + s_lo), tolC = d.bounds[6];
+  // highest degree whose dynamic range the filter carries: the guard columns near lo are
+  // damped towards 1 / T_d(t_sc) relative to the column at the scaling point, and below
+  // the filter's noise (FP32-class 1e-7, BF16 1e-3, FP64 1e-12) they degenerate
+  int cap = cap0;
+  {
+    const double at = fabs((s_sc - c) / e);
+    const double kappa = d.flags[5] ? 1e12 : (d.nsplit == 3 ? 1e7 : 1e3);
+    if (at > 1.0) cap = max(deg_min, min(cap0, (int)floor(log(2.0 * kappa) / log(at + sqrt(at * at - 1.0)))));
+  }
   double need = (double)deg_min;
   for (int i = threadIdx.x; i < nev; i += blockDim.x) {
     double r = d.res[i];
     if (!(r <= tolC)) {
       double at = fabs((d.theta[i] - c) / e);
       if (at <= 1.0 || !(r < 1e300)) need = fmax(need, (double)cap);
-      else need = fmax(need, ceil(log(r / tolC) / log(at + sqrt(at * at - 1.0))));
+      else need = fmax(need, ceil(log(10.0 * r / tolC) / log(at + sqrt(at * at - 1.0))));   // 10x margin
     }
   }
   need = bmax_d(need, red);
@@ -806,6 +815,7 @@ __global__ void b_round_status(const BDesc* D, int* out) {
       d.flags[0] = 0;
       d.flags[12] = 1;
     } else if (!info && !d.flags[5] && mx > 0.25 * d.bounds[8] && d.bounds[8] < 1e300 &&
+               mx <= (d.nsplit == 3 ? 1e-3 : 1e-1) * d.bounds[7] &&   // below the cold-start zone
                mx > 25.0 * d.bounds[21]) {
       // the low-precision filter gained less than 4x where the Chebyshev factors of this
       // round promised more than 100x: it has reached its floor. The FP32-class floor

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -53,6 +54,21 @@ struct gevp_ctx {
   double *theta = nullptr, *res = nullptr, *dscale = nullptr, *partial = nullptr, *bounds = nullptr,
          *lam = nullptr, *resf = nullptr;
   int *info = nullptr, *flag = nullptr;
+  unsigned long long* vscratch = nullptr;   // matrix-variation reductions and thresholds
+  unsigned long long* vd2 = nullptr;        // matrix-variation squared moduli (grown on demand)
+  size_t vd2_bytes = 0;
+  char* dvbuf = nullptr;                    // deviation-angle scratch (grown on demand)
+  size_t dvbuf_bytes = 0;
+  // emulated FP64 products of the reduction (digit form of L^-1 for both roles, and per
+  // stream the digit forms of tril(A) and of T = L^-1 tril(A)); grown on demand
+  int oz_slices = 0;                        // 0: FP64 pipe; 1..8: emulated with that many digits
+  char* ozmem[2] = {nullptr, nullptr};      // [0] L^-1 operands + main-stream scratch, [1] side stream
+  size_t ozmem_bytes[2] = {0, 0};
+  gevp::OzOperand ozLA, ozLB, ozAB[2], ozTA[2];
+  int64_t oz_l_gen = -1;                    // chol_gen the L^-1 operands were split from
+  int oz_l_S = 0;
+  int64_t chol_gen = 0;                     // incremented by every factorisation of B
+  int* ozflags = nullptr;                   // device: [0] kernel error code, [1] non-finite entry
   // pinned host mirror
   double* hbuf = nullptr;
   size_t hbuf_elems = 0;
@@ -183,6 +199,7 @@ size_t layout(gevp_ctx* h, char* base, int64_t n, int m) {
   h->bounds = (double*)take(16 * 8);
   h->info = (int*)take(64);
   h->flag = (int*)take(64);
+  h->vscratch = (unsigned long long*)take(64 * 8);
   return off;
 }
 
@@ -287,6 +304,7 @@ gevp_status factor_B(gevp_ctx* h, int64_t n, const double2* B, int64_t ldb, int6
   }
   trtri_lower(n, h->L, n, h->Linv, n, h->trtri_ws, h->trtri_elems, h->stream, true);
   h->chol_valid = true;
+  ++h->chol_gen;
   return GEVP_OK;
 }
 
@@ -305,8 +323,77 @@ void reduce_into_ws(int64_t n, const double2* Linv, const double2* A, int64_t ld
   herm_sum_inplace(n, Cout, ldc, s);
 }
 
-void reduce_into(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, double2* Cout, int64_t ldc) {
+// The same reduction with the n^3 products emulated on the tensor cores (slices digits
+// per entry): T = L^-1 tril_half(A) and M = T L^-H as digit-form products, then C = M + M^H.
+// side 0 runs on the main stream, side 1 on the pipeline's side stream (own scratch). The
+// digit forms of L^-1 are made once per factorisation of B, on the main stream.
+// device scratch of the emulated products: ozmem[side] of at least `need` bytes
+gevp_status oz_reserve(gevp_ctx* h, int side, size_t need) {
+  if (!h->ozflags) {
+    void* p = nullptr;
+    CK(cudaMalloc(&p, 2 * sizeof(int)));
+    CK(cudaMemsetAsync(p, 0, 2 * sizeof(int), h->stream));
+    h->ozflags = (int*)p;
+  }
+  if (need <= h->ozmem_bytes[side]) return GEVP_OK;
+  // the other stream may still read this side's (or, for side 0, the shared) operands
+  cudaDeviceSynchronize();
+  if (h->ozmem[side]) cudaFree(h->ozmem[side]);
+  h->ozmem[side] = nullptr;
+  h->ozmem_bytes[side] = 0;
+  if (side == 0) h->oz_l_gen = -1;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, need));
+  h->ozmem[side] = (char*)p;
+  h->ozmem_bytes[side] = need;
+  return GEVP_OK;
+}
+
+gevp_status reduce_emulated(gevp_ctx* h, int side, int64_t n, const double2* A, int64_t lda, double2* Cout,
+                            int64_t ldc, double2* T, cudaStream_t s) {
+  const int S = h->oz_slices;
+  const int nn = (int)n;
+  const size_t bA = gevp::oz_operand_bytes(nn, nn, S, 2), bB = gevp::oz_operand_bytes(nn, nn, S, 3);
+  TRY(oz_reserve(h, side, (side == 0 ? bA + bB : 0) + bA + bB));
+  char* mem = h->ozmem[side];
+  if (side == 0 && (h->oz_l_gen != h->chol_gen || h->oz_l_S != S)) {
+    // L^-1 as the left operand (rows, lower) and L^-H as the right one (rows of L^-1, conjugated)
+    CK(gevp::oz_split(h->ozLA, mem, nn, nn, h->Linv, n, 0, 2, S, 2, h->ozflags + 1, h->stream));
+    CK(gevp::oz_split(h->ozLB, mem + bA, nn, nn, h->Linv, n, 1, 2, S, 3, h->ozflags + 1, h->stream));
+    h->oz_l_gen = h->chol_gen;
+    h->oz_l_S = S;
+  }
+  if (side == 0) mem += bA + bB;
+  // columns of tril_half(A) are the conjugated rows of the Hermitian A from the diagonal on
+  CK(gevp::oz_split(h->ozAB[side], mem, nn, nn, A, lda, 1, 1, S, 3, h->ozflags + 1, s));
+  CK(gevp::oz_gemm(h->ozLA, h->ozAB[side], 1, 1, T, n, h->ozflags, s));
+  CK(gevp::oz_split(h->ozTA[side], mem + bB, nn, nn, T, n, 0, 2, S, 2, h->ozflags + 1, s));
+  CK(gevp::oz_gemm(h->ozTA[side], h->ozLB, 1, 2, Cout, ldc, h->ozflags, s));
+  herm_sum_inplace(n, Cout, ldc, s);
+  return GEVP_OK;
+}
+
+gevp_status reduce_into(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, double2* Cout, int64_t ldc) {
+  if (h->oz_slices > 0) return reduce_emulated(h, 0, n, A, lda, Cout, ldc, h->T, h->stream);
   reduce_into_ws(n, h->Linv, A, lda, Cout, ldc, h->T, h->split, h->split_elems, h->stream);
+  return GEVP_OK;
+}
+
+// error code of an emulated-product kernel since the last check (0: none), then cleared
+gevp_status oz_check(gevp_ctx* h) {
+  if (!h->ozflags) return GEVP_OK;
+  int f[2] = {0, 0};
+  CK(cudaMemcpyAsync(f, h->ozflags, sizeof f, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (f[0] == 0 && f[1] == 0) return GEVP_OK;
+  CK(cudaMemsetAsync(h->ozflags, 0, 2 * sizeof(int), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (f[0] != 0) {
+    h->err = "a bounded wait of the emulated FP64 product ran out";
+    return GEVP_ERR_TIMEOUT;
+  }
+  h->err = "NaN or Inf in an operand of the emulated FP64 product";
+  return GEVP_ERR_INVALID_VALUE;
 }
 
 // Streams and buffers of the sequence pipeline (sized from the main arena's n and split).
@@ -485,6 +572,12 @@ gevp_status lanczos(gevp_ctx* h, int64_t n, const double2* M, int64_t ldm, int k
   return sync_read(h, h->bounds, host_out, 5 * sizeof(double));
 }
 
+// GEVP_TRACE set in the environment: one line per solver round on stderr
+bool trace_on() {
+  static const bool on = std::getenv("GEVP_TRACE") != nullptr;
+  return on;
+}
+
 struct SolveState {
   int m, nev;
   int nlock = 0;
@@ -503,10 +596,26 @@ int choose_degree(const SolveState& S, double lo, double hi, double tolC, int dm
     double at = std::fabs(t);
     if (at <= 1.0) { d = dmax; break; }
     double rho = at + std::sqrt(at * at - 1.0);
-    int di = (int)std::ceil(std::log(r / tolC) / std::log(rho));
+    // aim 10x below the tolerance: a degree that only just reaches it leaves the pairs
+    // closest to the damped interval crawling over several extra rounds
+    int di = (int)std::ceil(std::log(10.0 * r / tolC) / std::log(rho));
     d = std::max(d, di);
   }
   return std::min(std::max(d, dmin), dmax);
+}
+
+// Highest degree whose dynamic range the filter can carry. The scaled filter keeps the
+// column at the scaling point sc at 1 and damps the guard columns near lo towards
+// 1 / T_d(t_sc); once that falls below the filter's relative noise, the guard columns
+// degenerate into noise and the last wanted pairs (which need them) stop converging.
+// kappa ~ the inverse noise level of the filter's arithmetic: FP32-class 1e7, BF16 1e3,
+// FP64 1e12 (CholQR's limit).
+int range_degree_cap(double sc, double lo, double hi, int prec) {
+  const double e = 0.5 * (hi - lo), c = 0.5 * (hi + lo);
+  const double at = std::fabs((sc - c) / e);
+  if (!(at > 1.0)) return 1 << 20;
+  const double kappa = prec == GEVP_PREC_FP32 ? 1e7 : (prec == GEVP_PREC_BF16 ? 1e3 : 1e12);
+  return (int)std::floor(std::log(2.0 * kappa) / std::log(at + std::sqrt(at * at - 1.0)));
 }
 
 // Largest residual among the unlocked wanted pairs that Chebyshev theory predicts after a
@@ -617,7 +726,8 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     double sc = S.have_theta ? std::min(S.theta[0], S.lower_est) : S.lower_est;
     if (!(lo > sc + 1e-3 * (hi - sc))) lo = sc + 0.5 * (hi - sc);
     if (!(hi > lo)) hi = lo + 1e-3 * S.normC + 1e-300;
-    int deg = S.have_theta ? choose_degree(S, lo, hi, tolC, o.deg_min, deg_cap) : std::min(deg_cap, 10);
+    const int cap = std::max(o.deg_min, std::min(deg_cap, range_degree_cap(sc, lo, hi, prec)));
+    int deg = S.have_theta ? choose_degree(S, lo, hi, tolC, o.deg_min, cap) : std::min(cap, 10);
     const double pred = S.have_theta ? predicted_max_res(S, lo, hi, tolC, deg) : 0.0;
     double2* Yf;
     if (prec != GEVP_PREC_FP64) {
@@ -656,7 +766,13 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     // progress in a round where the Chebyshev factors promised more than 100x) -> FP64
     // for the rest of this problem. Slow progress that theory predicts (Ritz values close
     // to the damped interval) is no reason to switch: FP64 would not converge faster.
-    if (prec != GEVP_PREC_FP64 && mr > 0.25 * prev_maxres && (pred <= 0.0 || mr > 25.0 * pred)) {
+    // The prediction assumes settled Ritz values; while residuals are still large (the
+    // first rounds of a cold start) it is no test of the filter's precision, so a stall
+    // only counts below 1e-3 ||C|| for the FP32-class filter (its floor is near 1e-8) and
+    // below 1e-1 ||C|| for BF16.
+    const double stall_zone = (prec == GEVP_PREC_FP32 ? 1e-3 : 1e-1) * S.normC;
+    if (prec != GEVP_PREC_FP64 && mr <= stall_zone && mr > 0.25 * prev_maxres &&
+        (pred <= 0.0 || mr > 25.0 * pred)) {
       // The FP32-class filter's floor depends on the degree (its rounding is amplified
       // along the recurrence): first halve the degree cap, down to 16; BF16's floor does
       // not depend on it, so BF16 switches at once.
@@ -667,6 +783,9 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
         if (st) st->switches++;
       }
     }
+    if (trace_on())
+      std::fprintf(stderr, "gevp: problem %d round %d prec %d deg %d cap %d lo %.6g hi %.6g sc %.6g nlock %d maxres %.3e "
+                   "pred %.3e zone %.3e\n", prob_index, it, prec, deg, cap, lo, hi, sc, S.nlock, mr, pred, stall_zone);
     prev_maxres = mr;
   }
   if (st) {
@@ -698,7 +817,10 @@ gevp_status prefetch_problem(gevp_ctx* h, int64_t n, int m, const double2* A, in
                              int idx) {
   CK(cudaEventRecord(h->ev_main, h->stream));
   CK(cudaStreamWaitEvent(h->side, h->ev_main, 0));
-  reduce_into_ws(n, h->Linv, A, lda, h->C2, n, h->T2, h->split2, h->split2_elems, h->side);
+  if (h->oz_slices > 0)
+    TRY(reduce_emulated(h, 1, n, A, lda, h->C2, n, h->T2, h->side));
+  else
+    reduce_into_ws(n, h->Linv, A, lda, h->C2, n, h->T2, h->split2, h->split2_elems, h->side);
   z_to_c(n, n, h->C2, n, h->M32b, n, h->side);
   lanczos_bounds(n, h->M32b, n, o.lanczos_steps, m, o.seed + 7919ull * idx, h->lw2, h->bounds2, h->side);
   z_to_c(n, n, A, lda, h->M32b, n, h->side);
@@ -800,6 +922,11 @@ gevp_status gevp_destroy(gevp_handle h) {
   if (h->tc2) gevp::filter_tc_release(h->tc2);
   if (h->batch) gevp::batch_release(h->batch);
   if (h->parena) cudaFree(h->parena);
+  if (h->vd2) cudaFree(h->vd2);
+  if (h->dvbuf) cudaFree(h->dvbuf);
+  for (int i = 0; i < 2; ++i)
+    if (h->ozmem[i]) cudaFree(h->ozmem[i]);
+  if (h->ozflags) cudaFree(h->ozflags);
   if (h->hb2) cudaFreeHost(h->hb2);
   for (cudaEvent_t e : {h->ev_main, h->ev_side, h->ev_user})
     if (e) cudaEventDestroy(e);
@@ -830,7 +957,7 @@ gevp_status gevp_reduce(gevp_handle h, int64_t n, const void* A, int64_t lda, co
   cudaSetDevice(h->device);
   TRY(ensure(h, n, 1));
   TRY(factor_B(h, n, (const double2*)B, ldb, info));
-  reduce_into(h, n, (const double2*)A, lda, (double2*)C, ldc);
+  TRY(reduce_into(h, n, (const double2*)A, lda, (double2*)C, ldc));
   zcopy2d(n, n, h->L, n, (double2*)L, ldl, h->stream);
   h->chol_valid = false;   // the caller's next solve refactors
   CK(cudaStreamSynchronize(h->stream));
@@ -863,9 +990,19 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
   if (o.deg_min < 1) o.deg_min = 1;
   if (o.deg_max < o.deg_min) o.deg_max = o.deg_min;
   if (o.lanczos_steps < 4) o.lanczos_steps = 4;
+  if (o.reduce_slices < 0 || o.reduce_slices > gevp::kOzSlicesMax) return GEVP_ERR_INVALID_ARG;
+  if (o.reduce_slices > 0 && !gevp::oz_supported()) {
+    h->err = "emulated FP64 products need an sm_103 device";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  if (o.reduce_slices > 0 && n > 30720) {
+    h->err = "emulated product: n above 30720";
+    return GEVP_ERR_UNSUPPORTED;
+  }
   for (int l = 0; l < nprob; ++l)
     if (!A[l] || !B[l]) return GEVP_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
+  h->oz_slices = o.reduce_slices;
   TRY(ensure(h, n, m));
   TRY(ensure_pipeline(h));
   PipelineScope pipe(h);
@@ -883,6 +1020,9 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
   gevp_status overall = GEVP_OK;
   bool warm_ok = false;   // Q holds a usable start block for this n, m
   bool have_pre = false;  // C2 / bounds2 / tc2 hold problem l's standard form
+  int64_t cold_mv = -1;   // filter matvecs of the latest cold-started problem
+  int flat = 0;           // consecutive warm problems that saved nothing over it
+  bool refresh = false;   // the next problem starts cold
   for (int l = 0; l < nprob; ++l) {
     Timer tm(h);
     tm.start();
@@ -921,7 +1061,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
       pipe.swap_buffers();
       have_pre = false;
     } else {
-      reduce_into(h, n, Al, lda, h->C, n);
+      TRY(reduce_into(h, n, Al, lda, h->C, n));
     }
     st->flops_fp64 += 4.0 * (double)n * n * n;
     tm.mark(PH_REDUCE);
@@ -931,7 +1071,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
       have_pre = true;
     }
     bool warm = false;
-    if (!o.cold_start) {
+    if (!o.cold_start && !refresh) {
       if (l == 0 && X_prev) {
         // seed from the caller's vectors: Y0[:, :kprev] = L^H X_prev, rest random
         zrandn(n, m, h->Y1, ld, o.seed + 17, h->stream);
@@ -955,6 +1095,19 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
     if (s != GEVP_OK && s != GEVP_ERR_NO_CONVERGENCE) return s;
     if (s == GEVP_ERR_NO_CONVERGENCE) overall = s;
     warm_ok = true;
+    st->cold = warm ? 0 : 1;
+    if (o.refresh_window > 0) {
+      // refresh: warm starts that no longer save filter work over the latest cold solve
+      if (!warm) {
+        cold_mv = st->matvecs;
+        flat = 0;
+        refresh = false;
+      } else if (cold_mv >= 0 && st->matvecs >= cold_mv) {
+        if (++flat >= o.refresh_window) refresh = true;
+      } else {
+        flat = 0;
+      }
+    }
     CK(cudaStreamSynchronize(h->stream));
     CK(cudaGetLastError());
     tm.mark(PH_FINAL);
@@ -972,6 +1125,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
     for (int p = 0; p < PH_N; ++p) tot += tm.ms[p];
     st->ms_total = tot;
   }
+  if (h->oz_slices > 0) TRY(oz_check(h));
   if (overall != GEVP_OK) h->err = "some residual stayed above tol";
   return overall;
 }
@@ -1161,6 +1315,218 @@ gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* 
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return GEVP_OK;
+}
+
+gevp_status gevp_matrix_variation(gevp_handle h, int64_t n, const void* A_new, int64_t lda, const void* A_old,
+                                  int64_t ldb, int nthr, const double* p_t, double* delta, int64_t* counts,
+                                  void* mask) {
+  if (!h || n < 0 || !delta || nthr < 0 || nthr > variation_max_thresholds()) return GEVP_ERR_INVALID_ARG;
+  if (nthr > 0 && (!p_t || !counts)) return GEVP_ERR_INVALID_ARG;
+  *delta = 0.0;
+  for (int t = 0; t < nthr; ++t) counts[t] = 0;
+  if (n == 0) return GEVP_OK;
+  if (!A_new || !A_old || bad_ld(lda, n) || bad_ld(ldb, n)) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, std::max<int64_t>(1, h->cap_n), std::max(1, h->cap_m)));
+  unsigned long long* ws = h->vscratch;
+  double* p_dev = (double*)(ws + 32);
+  const size_t need = (size_t)n * n * sizeof(unsigned long long);
+  if (need > h->vd2_bytes) {
+    if (h->vd2) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->vd2);
+      h->vd2 = nullptr;
+      h->vd2_bytes = 0;
+    }
+    void* p = nullptr;
+    CK(cudaMalloc(&p, need));
+    h->vd2 = (unsigned long long*)p;
+    h->vd2_bytes = need;
+  }
+  CK(cudaMemsetAsync(ws, 0, 32 * sizeof(unsigned long long), h->stream));
+  if (nthr > 0) CK(cudaMemcpyAsync(p_dev, p_t, nthr * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  gevp::matrix_variation(n, (const double2*)A_new, lda, (const double2*)A_old, ldb, nthr, p_dev, ws, h->vd2,
+                         (uint8_t*)mask, h->stream);
+  unsigned long long out[32];
+  TRY(sync_read(h, ws, out, sizeof(out)));
+  if (out[1] != 0) {
+    h->err = "NaN in a matrix difference";
+    return GEVP_ERR_INVALID_VALUE;
+  }
+  double dmax2;
+  std::memcpy(&dmax2, &out[0], sizeof(double));
+  *delta = std::sqrt(dmax2);
+  for (int t = 0; t < nthr; ++t) counts[t] = (int64_t)out[2 + t];
+  return GEVP_OK;
+}
+
+gevp_status gevp_deviation_angles(gevp_handle h, int64_t n, int k_old, int k_new, const void* X_old, int64_t ldo,
+                                  const void* X_new, int64_t ldn, const void* B, int64_t ldb, const double* lam_old,
+                                  const double* lam_new, double window, double* cosines, int64_t ldc, int64_t* perm,
+                                  double* theta, double* cost, int64_t* n_outside) {
+  if (!h || n < 0 || k_old < 0 || k_new < k_old || !(window >= 0.0)) return GEVP_ERR_INVALID_ARG;
+  const bool windowed = std::isfinite(window);
+  if (windowed && (!lam_old || !lam_new)) return GEVP_ERR_INVALID_ARG;
+  if (cost) *cost = 0.0;
+  if (n_outside) *n_outside = 0;
+  if (k_old == 0) return GEVP_OK;
+  if (n == 0 || !X_old || !X_new || bad_ld(ldo, k_old) || bad_ld(ldn, k_new)) return GEVP_ERR_INVALID_ARG;
+  if ((B && bad_ld(ldb, n)) || (cosines && bad_ld(ldc, k_new))) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  TRY(ensure(h, std::max<int64_t>(1, h->cap_n), std::max(1, h->cap_m)));
+  const int64_t ko = k_old, kn = k_new;
+  const int slices = gevp::deviation_norm_slices(n);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t wbytes = B ? up((size_t)n * (ko + kn) * sizeof(double2)) : 0;
+  const size_t obytes = up((size_t)ko * kn * sizeof(double2));
+  const size_t cbytes = up((size_t)ko * kn * sizeof(double));
+  const size_t pbytes = up((size_t)slices * kn * sizeof(double));
+  const size_t nbytes = up((size_t)(ko + kn) * sizeof(double));
+  const size_t need = wbytes + obytes + cbytes + pbytes + nbytes + 256;
+  if (need > h->dvbuf_bytes) {
+    if (h->dvbuf) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->dvbuf);
+      h->dvbuf = nullptr;
+      h->dvbuf_bytes = 0;
+    }
+    void* p = nullptr;
+    CK(cudaMalloc(&p, need));
+    h->dvbuf = (char*)p;
+    h->dvbuf_bytes = need;
+  }
+  char* q = h->dvbuf;
+  double2* Wo = (double2*)q;
+  double2* Wn = Wo + (size_t)n * ko;
+  q += wbytes;
+  double2* O = (double2*)q;
+  q += obytes;
+  double* cosb = (double*)q;
+  q += cbytes;
+  double* part = (double*)q;
+  q += pbytes;
+  double* nrm = (double*)q;
+  q += nbytes;
+  int* bad = (int*)q;
+  const double2* Xo = (const double2*)X_old;
+  const double2* Xn = (const double2*)X_new;
+  const double2* Wop = Xo;
+  const double2* Wnp = Xn;
+  int64_t ldwo = ldo, ldwn = ldn;
+  if (B) {
+    // W = B X for both blocks (FP64 complex GEMMs); with B = I the blocks are their own W
+    gevp::zgemm(gevp::zg((int)n, (int)ko, (int)n, (const double2*)B, ldb, 0, Xo, ldo, 0, Wo, ko), h->split,
+                h->split_elems, h->stream);
+    gevp::zgemm(gevp::zg((int)n, (int)kn, (int)n, (const double2*)B, ldb, 0, Xn, ldn, 0, Wn, kn), h->split,
+                h->split_elems, h->stream);
+    Wop = Wo;
+    Wnp = Wn;
+    ldwo = ko;
+    ldwn = kn;
+  }
+  // O = X_old^H (B X_new), the B-norms, the cosine table
+  gevp::zgemm(gevp::zg((int)ko, (int)kn, (int)n, Xo, ldo, 1, Wnp, ldwn, 0, O, kn), h->split, h->split_elems,
+              h->stream);
+  gevp::column_bnorms(n, (int)ko, Xo, ldo, Wop, ldwo, part, nrm, h->stream);
+  gevp::column_bnorms(n, (int)kn, Xn, ldn, Wnp, ldwn, part, nrm + ko, h->stream);
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
+  gevp::overlap_cosines((int)ko, (int)kn, O, kn, nrm, nrm + ko, cosb, kn, bad, h->stream);
+  CK(cudaGetLastError());
+  if (cosines)
+    CK(cudaMemcpy2DAsync(cosines, ldc * sizeof(double), cosb, kn * sizeof(double), kn * sizeof(double), ko,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  int hbad = 0;
+  TRY(sync_read(h, bad, &hbad, sizeof(int)));
+  if (hbad) {
+    h->err = "an eigenvector has a B-norm that is zero or not finite";
+    return GEVP_ERR_INVALID_VALUE;
+  }
+  if (!perm && !theta && !cost && !n_outside) return GEVP_OK;
+  std::vector<double> c((size_t)ko * kn);
+  TRY(sync_read(h, cosb, c.data(), c.size() * sizeof(double)));
+  auto outside = [&](int64_t i, int64_t j) { return windowed && std::fabs(lam_old[i] - lam_new[j]) > window; };
+  std::vector<int64_t> match(ko);
+  if (perm) {
+    // a pair outside the window costs more than any assignment of pairs inside it
+    const double far = (double)ko + 1.0;
+    std::vector<double> w((size_t)ko * kn);
+    for (int64_t i = 0; i < ko; ++i)
+      for (int64_t j = 0; j < kn; ++j) w[i * kn + j] = outside(i, j) ? far : 1.0 - c[i * kn + j];
+    gevp::assign_min_cost((int)ko, (int)kn, w.data(), match.data());
+    for (int64_t i = 0; i < ko; ++i) perm[i] = match[i];
+  } else {
+    for (int64_t i = 0; i < ko; ++i) match[i] = i;
+  }
+  double tot = 0.0;
+  int64_t nout = 0;
+  const double half_pi = 2.0 * std::atan(1.0);
+  for (int64_t i = 0; i < ko; ++i) {
+    const double ci = c[i * kn + match[i]];
+    if (theta) theta[i] = std::acos(ci) / half_pi;
+    if (outside(i, match[i])) ++nout;
+    else tot += 1.0 - ci;
+  }
+  if (cost) *cost = tot;
+  if (n_outside) *n_outside = nout;
+  return GEVP_OK;
+}
+
+gevp_status gevp_assign_min_cost(int ko, int kn, const double* cost, int64_t* perm) {
+  if (ko < 0 || kn < ko || (ko > 0 && (!cost || !perm))) return GEVP_ERR_INVALID_ARG;
+  for (int64_t e = 0; e < (int64_t)ko * kn; ++e)
+    if (!std::isfinite(cost[e])) return GEVP_ERR_INVALID_ARG;
+  if (ko > 0) gevp::assign_min_cost(ko, kn, cost, perm);
+  return GEVP_OK;
+}
+
+gevp_status gevp_zgemm_emulated(gevp_handle h, int M, int N, int K, const void* A, int64_t lda, const void* B,
+                                int64_t ldb, void* D, int64_t ldd, int slices) {
+  if (!h || M < 0 || N < 0 || K < 0 || slices < 1 || slices > gevp::kOzSlicesMax) return GEVP_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return GEVP_OK;
+  if (!D || bad_ld(ldd, N)) return GEVP_ERR_INVALID_ARG;
+  if (K > 0 && (!A || !B || bad_ld(lda, K) || bad_ld(ldb, K))) return GEVP_ERR_INVALID_ARG;
+  if (K > 30720) {
+    h->err = "emulated product: K above 30720";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  cudaSetDevice(h->device);
+  if (!gevp::oz_supported()) {
+    h->err = "emulated FP64 products need an sm_103 device";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  if (K == 0) {
+    CK(cudaMemset2DAsync(D, ldd * sizeof(double2), 0, (size_t)N * sizeof(double2), M, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GEVP_OK;
+  }
+  const size_t bA = gevp::oz_operand_bytes(M, K, slices, 2), bB = gevp::oz_operand_bytes(N, K, slices, 3);
+  TRY(oz_reserve(h, 1, bA + bB));
+  gevp::OzOperand a, b;
+  CK(gevp::oz_split(a, h->ozmem[1], M, K, (const double2*)A, lda, 0, 0, slices, 2, h->ozflags + 1, h->stream));
+  CK(gevp::oz_split(b, h->ozmem[1] + bA, N, K, (const double2*)B, ldb, 1, 0, slices, 3, h->ozflags + 1,
+                    h->stream));
+  CK(gevp::oz_gemm(a, b, 0, 0, (double2*)D, ldd, h->ozflags, h->stream));
+  return oz_check(h);
+}
+
+gevp_status gevp_reduce_emulated(gevp_handle h, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                 void* L, int64_t ldl, void* C, int64_t ldc, int64_t* info, int slices) {
+  if (!h || slices < 1 || slices > gevp::kOzSlicesMax) return GEVP_ERR_INVALID_ARG;
+  if (n > 30720) {
+    h->err = "emulated product: n above 30720";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  cudaSetDevice(h->device);
+  if (n > 0 && !gevp::oz_supported()) {
+    h->err = "emulated FP64 products need an sm_103 device";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  const int keep = h->oz_slices;
+  h->oz_slices = slices;
+  gevp_status st = gevp_reduce(h, n, A, lda, B, ldb, L, ldl, C, ldc, info);
+  if (st == GEVP_OK) st = oz_check(h);
+  h->oz_slices = keep;
+  return st;
 }
 
 gevp_status gevp_probe_peaks(gevp_handle h, double* out) {

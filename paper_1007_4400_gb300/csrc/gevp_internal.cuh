@@ -252,6 +252,46 @@ struct TcgShape { int np, units, n_pad_max, ncols_pad_max, nchunk_max, steps; in
 cudaError_t tcg_prepare(int nchunk_max);
 cudaError_t tcg_filter(const BDesc* D, const TcgShape& g, int* err, cudaStream_t s);
 
+// ---------------------------------------------------------------- matrix variation
+int variation_max_thresholds();
+// ws: >= 48 words; [0] max of squared moduli (bits), [1] NaN flag, [2..] counts;
+// d2: n * n words of scratch
+void matrix_variation(int64_t n, const double2* A, int64_t lda, const double2* B, int64_t ldb, int nthr,
+                      const double* p_dev, unsigned long long* ws, unsigned long long* d2, uint8_t* mask,
+                      cudaStream_t s);
+
+// ---------------------------------------------------------------- emulated FP64 GEMM
+// An operand of the emulated product in digit form: `rows` rows of op(A) (npl = 2: planes
+// re, im) or columns of op(B) (npl = 3: re, im, -im), each K entries split into S base-128
+// digits, planes [npl][S][rows_pad][k_pad] BF16, followed by one exponent per row.
+constexpr int kOzSlicesMax = 8;
+struct OzOperand {
+  __nv_bfloat16* planes = nullptr;
+  int* ex = nullptr;
+  int rows = 0, K = 0, rows_pad = 0, k_pad = 0, S = 0, npl = 0;
+};
+size_t oz_operand_bytes(int rows, int K, int S, int npl);
+bool oz_supported();
+// rows of X (conj: conjugated; mask 1: k >= r with the diagonal halved, 2: k <= r) into
+// digit form in `mem` (oz_operand_bytes); *bad = 1 on a non-finite entry
+cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
+                     int S, int npl, int* bad, cudaStream_t s);
+// D (A.rows x B.rows) = op(A) op(B); triA 1: op(A) lower; triB 1: op(B) lower, 2: upper
+cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
+                    cudaStream_t s);
+
+// ---------------------------------------------------------------- deviation angles
+// slices of the column-norm reduction (part needs slices * k doubles)
+int deviation_norm_slices(int64_t n);
+// nrm2[j] = Re(x_j^H w_j) for the columns of X, W (n x k)
+void column_bnorms(int64_t n, int k, const double2* X, int64_t ldx, const double2* W, int64_t ldw, double* part,
+                   double* nrm2, cudaStream_t s);
+// c[i][j] = min(1, |O[i][j]| / sqrt(no2[i] nn2[j])); *bad = 1 on a norm that is not positive
+void overlap_cosines(int ko, int kn, const double2* O, int64_t ldo, const double* no2, const double* nn2, double* c,
+                     int64_t ldc, int* bad, cudaStream_t s);
+// host: minimum-cost assignment of the ko rows of a ko x kn (ko <= kn) table to distinct columns
+void assign_min_cost(int ko, int kn, const double* cost, int64_t* perm);
+
 // handle access for the translation units outside the main driver
 struct BatchPlan;
 void batch_release(BatchPlan* p);

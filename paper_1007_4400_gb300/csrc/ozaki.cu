@@ -1,0 +1,421 @@
+// FP64 complex matrix products emulated on the tcgen05 tensor cores (Ozaki scheme):
+// D = op(A) op(B) with FP64-class accuracy from exact BF16 products. On this part an SM
+// retires two FP64 FMAs per clock but thousands of BF16 tensor flops, so the n^3 products
+// of the reduction to standard form run far faster this way than on the FP64 pipe.
+//
+//  1. Splitting. Every row i of op(A) is scaled by 2^-e_i so that its largest real or
+//     imaginary part lies in [1/4, 1/2), rounded to the integer q = round(a 2^(7S))
+//     (|q| <= 2^(7S-1)) and written as S signed base-128 digits, a = 2^e_i sum_s d_s 2^-7s,
+//     |d_s| <= 64. Columns of op(B) likewise, with exponents f_j. Digits are small integers,
+//     exact in BF16. The rounding leaves at most 2^(e_i - 7S - 1) per entry.
+//  2. Digit products on the tensor cores. |d d'| <= 2^12, so an FP32 accumulation over at
+//     most 4096 products is exact (every partial sum is an integer of magnitude <= 2^24).
+//     The complex product is the real product of the embedding [[Ar, -Ai], [Ai, Ar]]
+//     [Br; Bi] = [Re; Im], 2K real terms per output, so K is cut into exact units of at
+//     most 2048 complex terms. Only digit pairs with s + t <= S + 1 are formed: the pairs
+//     left out weigh less than the rounding of step 1.
+//  3. Summation. The products of one level L = s + t share the scale 2^-7L and are summed
+//     exactly as 32-bit integers; the levels are combined by a Horner recurrence in FP64
+//     (one rounding per level), from the smallest level up, and the result is scaled by
+//     2^(e_i + f_j).
+// Error per entry, relative to 2^(e_i + f_j) <= 16 max_k|a_ik| max_k|b_kj|: about
+// 2K (S + 3) 2^(-7S - 2) in the worst case (K complex terms), the FP64 product's bound
+// K u sum_k |a_ik||b_kj| being of the same order for S = 8.
+//
+// GEMM kernel: one CTA per 128 x 128 tile of the real or the imaginary part of D. Warp 8
+// issues TMA loads (3D maps: k, row, digit; 128-byte swizzle; four stages), warp 9 issues
+// the MMAs of one unit (digit pair, K chunk) into one of two TMEM accumulators (128
+// columns each) while warps 0-7 drain the other: each thread owns one row and 64 columns,
+// converts the exact FP32 sums to integers and adds them up per level; at the end of a
+// level the FP64 Horner state, kept in the upper 256 TMEM columns, is updated. All waits
+// are bounded; on expiry the kernel records an error code, stops issuing work, frees its
+// TMEM and returns.
+#include "gevp_internal.cuh"
+#include "tc_ptx.cuh"
+#include <cuda.h>
+#include <algorithm>
+#include <cstring>
+
+namespace gevp {
+
+namespace {
+
+constexpr int OZ_TM = 128;
+constexpr int OZ_TN = 128;
+constexpr int OZ_TK = 64;
+constexpr int OZ_ST = 4;
+constexpr int OZ_KCHUNK = 2048;
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = (OZ_EPI_WARPS + 2) * 32;
+constexpr int OZ_MAXPAIRS = kOzSlicesMax * (kOzSlicesMax + 1) / 2;
+constexpr uint32_t OZ_TILE_BYTES = OZ_TM * OZ_TK * 2;   // one 128 x 64 BF16 box (A and B alike)
+constexpr size_t OZ_SMEM = (size_t)OZ_ST * 2 * OZ_TILE_BYTES + 1024;
+
+struct OzMaps {
+  CUtensorMap a[2];   // op(A) digit planes: re, im
+  CUtensorMap b[3];   // op(B)^T digit planes: re, im, -im
+};
+
+struct OzParams {
+  int M, N;        // complex output size
+  int mt;          // 128-row tiles of one part
+  int k_pad;       // padded K (multiple of 64)
+  int S;           // digits per entry
+  int triA;        // 1: op(A)[i][k] = 0 for k > i
+  int triB;        // 1: op(B)[k][j] = 0 for k < j;  2: op(B)[k][j] = 0 for k > j
+  const int* ea;   // row exponents of op(A)
+  const int* eb;   // column exponents of op(B)
+  double2* D;
+  int64_t ldd;
+  int* err;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[OZ_ST], empty[OZ_ST], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_sh;
+  __shared__ uint8_t pair_s[OZ_MAXPAIRS], pair_t[OZ_MAXPAIRS], pair_last[OZ_MAXPAIRS];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int part = blockIdx.y / p.mt;   // 0: real part of D, 1: imaginary part
+  const int m0 = (blockIdx.y % p.mt) * OZ_TM;
+  const int n0 = blockIdx.x * OZ_TN;
+  // K range of the tile from the triangular structure, in whole 64-blocks
+  int klo = 0, khi = p.k_pad;
+  if (p.triA == 1) khi = min(khi, m0 + OZ_TM);
+  if (p.triB == 1) klo = max(klo, n0);
+  if (p.triB == 2) khi = min(khi, n0 + OZ_TN);
+  const int klen = max(0, khi - klo);
+  const int nchunk = (klen + OZ_KCHUNK - 1) / OZ_KCHUNK;
+  const int npairs = p.S * (p.S + 1) / 2;
+  const int nunits = npairs * nchunk;
+  auto chunk_blocks = [&](int c) {   // 64-blocks of chunk c (one part of the embedding)
+    const int a = klo + c * OZ_KCHUNK;
+    return (min(khi, a + OZ_KCHUNK) - a) / OZ_TK;
+  };
+
+  if (threadIdx.x == 0) {
+    // pairs by level L = s + t from S + 1 down to 2, s ascending inside a level
+    int i = 0;
+    for (int L = p.S + 1; L >= 2; --L)
+      for (int s = 1; s < L; ++s, ++i) {
+        pair_s[i] = (uint8_t)s;
+        pair_t[i] = (uint8_t)(L - s);
+        pair_last[i] = (uint8_t)(s == L - 1);
+      }
+    for (int s = 0; s < OZ_ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], OZ_EPI_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_sh;
+
+  if (warp == OZ_EPI_WARPS && lane == 0) {
+    // producer: for block kh (embedding half) of a unit, the real-part tile multiplies
+    // A planes re | im with B planes re | -im, the imaginary-part tile im | re with re | im
+    int it = 0;
+    bool ok = true;
+    for (int u = 0; u < nunits && ok; ++u) {
+      const int pi = u / nchunk, c = u % nchunk;
+      const int sa = pair_s[pi] - 1, tb = pair_t[pi] - 1;
+      const int nb = chunk_blocks(c);
+      const int kbase = klo + c * OZ_KCHUNK;
+      for (int i = 0; i < 2 * nb; ++i, ++it) {
+        const int st = it % OZ_ST;
+        if (it >= OZ_ST && !mbar_wait(&empty[st], ((uint32_t)(it / OZ_ST) & 1u) ^ 1u, p.err, 21)) {
+          ok = false;
+          break;
+        }
+        const int kh = i / nb, kx = kbase + (i % nb) * OZ_TK;
+        const int pa = part ^ kh;
+        const int pb = kh == 0 ? 0 : (part == 0 ? 2 : 1);
+        uint8_t* sa_tile = smem + (size_t)st * 2 * OZ_TILE_BYTES;
+        mbar_expect_tx(&full[st], 2 * OZ_TILE_BYTES);
+        tma_load_3d(sa_tile, &maps.a[pa], kx, m0, sa, &full[st]);
+        tma_load_3d(sa_tile + OZ_TILE_BYTES, &maps.b[pb], kx, n0, tb, &full[st]);
+      }
+    }
+  } else if (warp == OZ_EPI_WARPS + 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(OZ_TM, OZ_TN);
+    int it = 0;
+    bool ok = true;
+    for (int u = 0; u < nunits && ok; ++u) {
+      const int buf = u & 1;
+      if (u >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((u >> 1) - 1) & 1u, p.err, 22)) break;
+      fence_after();
+      const uint32_t dt = tmem + (uint32_t)(buf * OZ_TN);
+      const int nb2 = 2 * chunk_blocks(u % nchunk);
+      for (int i = 0; i < nb2; ++i, ++it) {
+        const int st = it % OZ_ST;
+        if (!mbar_wait(&full[st], (uint32_t)(it / OZ_ST) & 1u, p.err, 23)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint8_t* base = smem + (size_t)st * 2 * OZ_TILE_BYTES;
+        const uint64_t da = sdesc(su32(base)), db = sdesc(su32(base + OZ_TILE_BYTES));
+#pragma unroll
+        for (int kk = 0; kk < OZ_TK / 16; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;
+          umma(dt, da + off, db + off, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        }
+        umma_commit(&empty[st]);
+      }
+      if (!ok) break;
+      umma_commit(&tfull[buf]);
+    }
+  } else if (warp < OZ_EPI_WARPS) {
+    const int q = warp & 3, ch = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const uint32_t col0 = (uint32_t)(ch * 64);
+    const uint32_t hcol = 256u + 2u * col0;   // FP64 Horner state: 2 TMEM columns per value
+    const int row = m0 + q * 32 + lane;
+    const bool row_ok = row < p.M;
+    const int er = row_ok ? p.ea[row] : 0;
+    double* Dd = (double*)p.D;
+    int acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    bool first_level = true, ok = true;
+    for (int u = 0; u < nunits; ++u) {
+      const int buf = u & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(u >> 1) & 1u, p.err, 24) ? 1 : 0) != 0;
+      if (!ok) break;
+      fence_after();
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        uint32_t r[16];
+        tmem_ld16(tmem + lane_base + (uint32_t)(buf * OZ_TN) + col0 + 16u * g, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[16 * g + j] += __float2int_rn(__uint_as_float(r[j]));
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      const int pi = u / nchunk;
+      if (u % nchunk != nchunk - 1 || !pair_last[pi]) continue;
+      // end of a level: h <- h 2^-7 + I_L (FP64), kept in TMEM until the last level
+      const bool last_level = (pi == npairs - 1);
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        uint32_t hv[16];
+        if (!first_level) {
+          tmem_ld16(tmem + lane_base + hcol + 16u * g, hv);
+          tmem_wait_ld();
+        }
+        double h8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const double prev = first_level ? 0.0 : __hiloint2double((int)hv[2 * j + 1], (int)hv[2 * j]);
+          h8[j] = fma(prev, 0x1p-7, (double)acc[8 * g + j]);
+          acc[8 * g + j] = 0;
+        }
+        if (!last_level) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            hv[2 * j] = (uint32_t)__double2loint(h8[j]);
+            hv[2 * j + 1] = (uint32_t)__double2hiint(h8[j]);
+          }
+          tmem_st16(tmem + lane_base + hcol + 16u * g, hv);
+        } else if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = n0 + (int)col0 + 8 * g + j;
+            if (col < p.N) Dd[2 * ((int64_t)row * p.ldd + col) + part] = ldexp(h8[j], er + p.eb[col] - 14);
+          }
+        }
+      }
+      if (!last_level) tmem_wait_st();
+      first_level = false;
+    }
+    if (nunits == 0 && row_ok) {
+      for (int j = 0; j < 64; ++j) {
+        const int col = n0 + (int)col0 + j;
+        if (col < p.N) Dd[2 * ((int64_t)row * p.ldd + col) + part] = 0.0;
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// Digits of one row (a row of op(A), or a column of op(B) read as a row of the stored
+// matrix): entry k of row r is X[r][k], conjugated if conj; mask 1 keeps k >= r with the
+// diagonal halved (a column of the lower triangle of a Hermitian matrix, tril(A) with its
+// diagonal split between A and A^H), mask 2 keeps k <= r. Writes the exponent of the row
+// and the S digits of the real part, the imaginary part and (npl = 3) the negated
+// imaginary part into planes [npl][S][rows_pad][k_pad]; rows and columns past the matrix
+// are zero. A row with a non-finite entry sets *bad.
+__device__ __forceinline__ double2 oz_entry(const double2* X, int64_t ldx, int r, int k, int K, int conj, int mask) {
+  if (k >= K) return make_double2(0.0, 0.0);
+  if ((mask == 1 && k < r) || (mask == 2 && k > r)) return make_double2(0.0, 0.0);
+  double2 v = X[(int64_t)r * ldx + k];
+  if (conj) v.y = -v.y;
+  if (mask == 1 && k == r) v = make_double2(0.5 * v.x, 0.5 * v.y);
+  return v;
+}
+
+__device__ __forceinline__ void oz_digits(double x, int shift, int S, __nv_bfloat16* out, size_t plane) {
+  long long q = __double2ll_rn(ldexp(x, shift));
+  for (int s = S - 1; s >= 1; --s) {
+    const long long d = ((q + 64) & 127) - 64;
+    out[(size_t)s * plane] = __int2bfloat16_rn((int)d);
+    q = (q - d) >> 7;
+  }
+  out[0] = __int2bfloat16_rn((int)q);
+}
+
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, const double2* X, int64_t ldx, int conj,
+                                                            int mask, int S, int npl, int rows_pad, int k_pad,
+                                                            __nv_bfloat16* planes, int* ex, int* bad) {
+  __shared__ double red[8];
+  const int r = blockIdx.x;
+  double mx = 0.0;
+  bool nonfinite = false;
+  if (r < rows)
+    for (int k = threadIdx.x; k < K; k += 256) {
+      const double2 v = oz_entry(X, ldx, r, k, K, conj, mask);
+      const double a = fmax(fabs(v.x), fabs(v.y));
+      if (!(a <= 1.7976931348623157e308)) nonfinite = true;   // NaN or Inf
+      else mx = fmax(mx, a);
+    }
+  if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
+  // 2^e > 2 mx: the scaled row lies below 1/2
+  const int e = mx > 0.0 ? ilogb(mx) + 2 : 0;
+  if (threadIdx.x == 0 && r < rows) ex[r] = e;
+  const int shift = 7 * S - e;
+  const size_t plane = (size_t)rows_pad * k_pad;
+  const size_t pstride = (size_t)S * plane;
+  for (int k = threadIdx.x; k < k_pad; k += 256) {
+    const double2 v = r < rows ? oz_entry(X, ldx, r, k, K, conj, mask) : make_double2(0.0, 0.0);
+    const size_t o = (size_t)r * k_pad + k;
+    oz_digits(v.x, shift, S, planes + o, plane);
+    oz_digits(v.y, shift, S, planes + pstride + o, plane);
+    if (npl == 3) oz_digits(-v.y, shift, S, planes + 2 * pstride + o, plane);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn oz_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3D map over the digit planes of one part: (k, row, digit), box 64 x 128 x 1
+bool oz_map(CUtensorMap* map, void* base, int k_pad, int rows_pad, int S) {
+  EncodeTiledFn enc = oz_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * k_pad * 2};
+  cuuint32_t box[3] = {OZ_TK, OZ_TM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t oz_operand_bytes(int rows, int K, int S, int npl) {
+  const size_t rp = (size_t)(rows + OZ_TM - 1) / OZ_TM * OZ_TM;
+  const size_t kp = (size_t)(K + OZ_TK - 1) / OZ_TK * OZ_TK;
+  return (size_t)npl * S * rp * kp * 2 + ((size_t)rows * 4 + 255) / 256 * 256;
+}
+
+bool oz_supported() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && oz_encode() != nullptr;
+}
+
+cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
+                     int S, int npl, int* bad, cudaStream_t s) {
+  if (S < 1 || S > kOzSlicesMax || (npl != 2 && npl != 3)) return cudaErrorInvalidValue;
+  op.rows = rows;
+  op.K = K;
+  op.S = S;
+  op.npl = npl;
+  op.rows_pad = (rows + OZ_TM - 1) / OZ_TM * OZ_TM;
+  op.k_pad = (K + OZ_TK - 1) / OZ_TK * OZ_TK;
+  op.planes = (__nv_bfloat16*)mem;
+  op.ex = (int*)((char*)mem + (size_t)npl * S * op.rows_pad * op.k_pad * 2);
+  if (rows == 0) return cudaSuccess;
+  oz_split_rows_kernel<<<op.rows_pad, 256, 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
+                                                   op.planes, op.ex, bad);
+  LAUNCH_NOTE(1);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
+                    cudaStream_t s) {
+  if (A.K != B.K || A.S != B.S || A.npl != 2 || B.npl != 3 || A.k_pad != B.k_pad) return cudaErrorInvalidValue;
+  // the integer sums of one level hold at most S products of 2^24 per K chunk
+  if (A.k_pad > 15 * OZ_KCHUNK) return cudaErrorInvalidValue;
+  if (A.rows == 0 || B.rows == 0) return cudaSuccess;
+  OzMaps maps;
+  std::memset(&maps, 0, sizeof maps);
+  const size_t pa = (size_t)A.S * A.rows_pad * A.k_pad, pb = (size_t)B.S * B.rows_pad * B.k_pad;
+  for (int i = 0; i < 2; ++i)
+    if (!oz_map(&maps.a[i], A.planes + i * pa, A.k_pad, A.rows_pad, A.S)) return cudaErrorInvalidValue;
+  for (int i = 0; i < 3; ++i)
+    if (!oz_map(&maps.b[i], B.planes + i * pb, B.k_pad, B.rows_pad, B.S)) return cudaErrorInvalidValue;
+  OzParams p;
+  p.M = A.rows;
+  p.N = B.rows;
+  p.mt = A.rows_pad / OZ_TM;
+  p.k_pad = A.k_pad;
+  p.S = A.S;
+  p.triA = triA;
+  p.triB = triB;
+  p.ea = A.ex;
+  p.eb = B.ex;
+  p.D = D;
+  p.ldd = ldd;
+  p.err = err;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(B.rows_pad / OZ_TN, 2 * p.mt);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(maps, p);
+  LAUNCH_NOTE(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gevp

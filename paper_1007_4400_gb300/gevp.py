@@ -8,10 +8,12 @@ raises.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _build
@@ -36,14 +38,15 @@ class GevpOpts(C.Structure):
     _fields_ = [("filter_prec", C.c_int), ("tol", C.c_double), ("max_outer", C.c_int), ("deg_min", C.c_int),
                 ("deg_max", C.c_int), ("nex", C.c_int), ("seed", C.c_uint64), ("b_fixed", C.c_int),
                 ("cold_start", C.c_int), ("lanczos_steps", C.c_int), ("refine_iters", C.c_int),
-                ("keep_all_X", C.c_int)]
+                ("keep_all_X", C.c_int), ("refresh_window", C.c_int),
+                ("reduce_slices", C.c_int)]
 
 
 class GevpStats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("filter_steps", C.c_int), ("switches", C.c_int),
                 ("orth_fallbacks", C.c_int), ("final_passes", C.c_int), ("converged", C.c_int),
                 ("matvecs", C.c_int64), ("flops_fp64", C.c_double), ("flops_lowp", C.c_double),
-                ("max_resid", C.c_double), ("orth_err", C.c_double),
+                ("max_resid", C.c_double), ("orth_err", C.c_double), ("cold", C.c_int),
                 ("ms_chol", C.c_float), ("ms_reduce", C.c_float), ("ms_bounds", C.c_float),
                 ("ms_filter", C.c_float), ("ms_orth", C.c_float), ("ms_rr", C.c_float), ("ms_resid", C.c_float),
                 ("ms_final", C.c_float), ("ms_total", C.c_float)]
@@ -110,11 +113,21 @@ def load(build_if_missing: bool = True):
         L.gevp_spectral_bounds.argtypes = [vp, i64, vp, i64, i32, i32, C.POINTER(f64)]
         L.gevp_energy_backward.argtypes = [vp, i64, i32, vp, i64, vp, f64, vp, vp, i64]
         L.gevp_probe_peaks.argtypes = [vp, C.POINTER(f64)]
+        L.gevp_matrix_variation.argtypes = [vp, i64, vp, i64, vp, i64, i32, C.POINTER(f64), C.POINTER(f64),
+                                            C.POINTER(i64), vp]
+        L.gevp_deviation_angles.argtypes = [vp, i64, i32, i32, vp, i64, vp, i64, vp, i64, C.POINTER(f64),
+                                            C.POINTER(f64), f64, vp, i64, C.POINTER(i64), C.POINTER(f64),
+                                            C.POINTER(f64), C.POINTER(i64)]
+        L.gevp_assign_min_cost.argtypes = [i32, i32, C.POINTER(f64), C.POINTER(i64)]
+        L.gevp_zgemm_emulated.argtypes = [vp, i32, i32, i32, vp, i64, vp, i64, vp, i64, i32]
+        L.gevp_reduce_emulated.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, C.POINTER(i64), i32]
         L.gevp_kernel_launches.argtypes = [vp]
         L.gevp_kernel_launches.restype = i64
         for name in ("gevp_create", "gevp_destroy", "gevp_set_stream", "gevp_reduce", "gevp_solve_sequence",
                      "gevp_solve_sequence_host", "gevp_solve_batched", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
-                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_probe_peaks"):
+                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_probe_peaks",
+                     "gevp_matrix_variation", "gevp_deviation_angles", "gevp_assign_min_cost",
+                     "gevp_zgemm_emulated", "gevp_reduce_emulated"):
             getattr(L, name).restype = i32
         _LIB = L
         return L
@@ -168,18 +181,39 @@ def default_opts(**kw) -> GevpOpts:
     return o
 
 
-def reduce(A: torch.Tensor, B: torch.Tensor):
-    """(L, C) with B = L L^H and C = L^-1 A L^-H (see gevp_reduce)."""
+def reduce(A: torch.Tensor, B: torch.Tensor, slices: int = 0):
+    """(L, C) with B = L L^H and C = L^-1 A L^-H (see gevp_reduce). slices > 0: the n^3
+    products emulated on the tensor cores with that many digits (gevp_reduce_emulated)."""
     _mat(A, "A"); _mat(B, "B")
     n = A.shape[0]
     h = _handle(A.device)
     L_ = torch.empty_like(A)
     C_ = torch.empty_like(A)
     info = C.c_int64(0)
-    st = load().gevp_reduce(h, n, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(L_), n, _ptr(C_), n,
-                            C.byref(info))
+    if slices > 0:
+        st = load().gevp_reduce_emulated(h, n, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(L_), n, _ptr(C_),
+                                         n, C.byref(info), int(slices))
+    else:
+        st = load().gevp_reduce(h, n, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(L_), n, _ptr(C_), n,
+                                C.byref(info))
     _check(st, h)
     return L_, C_
+
+
+def zgemm_emulated(A: torch.Tensor, B: torch.Tensor, slices: int = 8) -> torch.Tensor:
+    """A B^H (A M x K, B N x K, complex128) emulated on the tensor cores with `slices`
+    7-bit digits per entry (gevp_zgemm_emulated)."""
+    _mat(A, "A"); _mat(B, "B")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B need the same number of columns")
+    h = _handle(A.device)
+    D = torch.empty((M, N), dtype=torch.complex128, device=A.device)
+    st = load().gevp_zgemm_emulated(h, M, N, K, _ptr(A), A.stride(0) if K else 1, _ptr(B), B.stride(0) if K else 1,
+                                    _ptr(D), max(N, 1), int(slices))
+    _check(st, h)
+    return D
 
 
 @dataclass
@@ -387,6 +421,67 @@ def energy_backward(X: torch.Tensor, Lambda: torch.Tensor, gE: float = 1.0):
                                      _ptr(GA), _ptr(GB), n)
     _check(st, h)
     return GA, GB
+
+
+def matrix_variation(A_new: torch.Tensor, A_old: torch.Tensor, thresholds=(0.1,), want_mask: bool = False):
+    """(delta, counts, mask) of gevp_matrix_variation: the largest entry variation between
+    two consecutive matrices and the number of entries varying by more than p * delta."""
+    _mat(A_new, "A_new"); _mat(A_old, "A_old")
+    n = A_new.shape[0]
+    h = _handle(A_new.device)
+    k = len(thresholds)
+    p = (C.c_double * max(k, 1))(*[float(x) for x in thresholds])
+    delta = C.c_double(0.0)
+    counts = (C.c_int64 * max(k, 1))()
+    mask = torch.empty((n, n), dtype=torch.uint8, device=A_new.device) if want_mask else None
+    st = load().gevp_matrix_variation(h, n, _ptr(A_new), A_new.stride(0), _ptr(A_old), A_old.stride(0), k, p,
+                                      C.byref(delta), counts, _ptr(mask))
+    _check(st, h)
+    return delta.value, [int(counts[i]) for i in range(k)], mask
+
+
+def deviation_angles(X_old: torch.Tensor, X_new: torch.Tensor, B: torch.Tensor = None, lam_old=None, lam_new=None,
+                     window: float = math.inf, reindex: bool = True, want_cosines: bool = False) -> dict:
+    """gevp_deviation_angles: the normalised deviation angles (1.00 = pi/2) between the old
+    and the new eigenvectors in the B inner product, after re-indexing the new ones against
+    the old (reindex=True) or column by column. Returns a dict with perm (None without
+    re-indexing), theta, cost, n_outside and cosines (device k_old x k_new, or None)."""
+    _mat(X_old, "X_old"); _mat(X_new, "X_new")
+    if B is not None:
+        _mat(B, "B")
+    n, ko = X_old.shape
+    kn = X_new.shape[1]
+    h = _handle(X_old.device)
+    f64p = C.POINTER(C.c_double)
+    if math.isfinite(window):
+        lo = (C.c_double * max(ko, 1))(*[float(x) for x in lam_old])
+        ln = (C.c_double * max(kn, 1))(*[float(x) for x in lam_new])
+    else:
+        lo = ln = None
+    cos = torch.empty((ko, kn), dtype=torch.float64, device=X_old.device) if want_cosines else None
+    perm = (C.c_int64 * max(ko, 1))() if reindex else None
+    theta = (C.c_double * max(ko, 1))()
+    cost = C.c_double(0.0)
+    nout = C.c_int64(0)
+    st = load().gevp_deviation_angles(h, n, ko, kn, _ptr(X_old), X_old.stride(0), _ptr(X_new), X_new.stride(0),
+                                      _ptr(B), B.stride(0) if B is not None else 0, lo, ln, float(window),
+                                      _ptr(cos), kn, perm, theta, C.byref(cost), C.byref(nout))
+    _check(st, h)
+    return {"perm": np.array(perm[:ko], dtype=np.int64) if reindex else None,
+            "theta": np.array(theta[:ko]), "cost": cost.value, "n_outside": int(nout.value), "cosines": cos}
+
+
+def assign_min_cost(cost) -> np.ndarray:
+    """gevp_assign_min_cost (host only): the column of each row in the minimum-cost
+    assignment of the rows of a ko x kn (ko <= kn) table to distinct columns."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    ko, kn = c.shape
+    perm = np.zeros(max(ko, 1), dtype=np.int64)
+    st = load().gevp_assign_min_cost(ko, kn, c.ctypes.data_as(C.POINTER(C.c_double)),
+                                     perm.ctypes.data_as(C.POINTER(C.c_int64)))
+    if st != 0:
+        raise ValueError(f"gevp_assign_min_cost: status {st}")
+    return perm[:ko]
 
 
 def probe_peaks(device=None) -> dict:

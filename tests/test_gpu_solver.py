@@ -159,3 +159,40 @@ def test_host_entry_point_matches_device(cuda):
     assert torch.equal(rh.Lambda, rd.Lambda.cpu())
     assert torch.equal(rh.resid, rd.resid.cpu())
     assert torch.equal(rh.X, rd.X.cpu())
+
+
+def _refresh_rule_holds(stats, window):
+    """Replays the refresh rule on the per-problem counters: after `window` consecutive warm
+    problems with at least the matvecs of the latest cold one, the next problem is cold."""
+    cold_mv, flat, refresh = -1, 0, False
+    for i, st in enumerate(stats):
+        if i > 0 and st["cold"] != (1 if refresh else 0):
+            return False
+        if st["cold"]:
+            cold_mv, flat, refresh = st["matvecs"], 0, False
+        elif cold_mv >= 0 and st["matvecs"] >= cold_mv:
+            flat += 1
+            refresh = flat >= window
+        else:
+            flat = 0
+    return True
+
+
+@pytest.mark.parametrize("eps0,decay", [(0.1, 0.6), (40.0, 1.0)])
+def test_refresh_policy(cuda, orc, eps0, decay):
+    """The slowly drifting SCF sequence never refreshes (every warm start saves work); a
+    sequence of unrelated problems (drift as large as the spectrum) follows the rule, and
+    every problem is solved to tolerance either way."""
+    from paper_1007_4400_gb300 import gevp, synth
+    n, nev, nex = 300, 16, 8
+    s = synth.make_sequence(1, n, 6, nev, nex, device=cuda, eps0=eps0, decay=decay)
+    r = gevp.solve_sequence(s.A, s.B, nev, nex=nex, refresh_window=1, keep_all_X=True)
+    assert r.status == 0
+    assert r.stats[0]["cold"] == 1
+    assert _refresh_rule_holds(r.stats, 1)
+    if eps0 < 1:
+        assert [st["cold"] for st in r.stats] == [1, 0, 0, 0, 0, 0]
+    B = s.B.cpu().numpy()
+    for l in (1, 5):
+        _check_problem(orc, s.A[l].cpu().numpy(), B, r.Lambda[l].cpu().numpy(), r.X[l].cpu().numpy(),
+                       r.resid[l].cpu().numpy(), nev, method="jacobi")

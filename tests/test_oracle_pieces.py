@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from tests.conftest import crandn, rand_herm
+from tests.conftest import crandn, rand_herm, rand_hpd
 
 
 def test_filter_closed_form_on_diagonal(orc):
@@ -127,3 +127,80 @@ def test_matrix_variation_invariants():
     diag_changed = np.count_nonzero(np.diag(A + 1e-3 * P) != np.diag(A))
     assert (counts[0] - diag_changed) % 2 == 0
     assert abs(delta - np.abs((A + 1e-3 * P) - A).max()) <= 1e-15 * delta
+
+
+def test_reindex_recovers_a_permutation():
+    """New eigenvectors that are a permuted, re-phased copy of the old: the assignment
+    returns the permutation and every matched angle is zero."""
+    from oracle import pieces
+    rng = np.random.default_rng(3)
+    n, k = 40, 9
+    B = rand_hpd(rng, n, cond=30.0)
+    X, _ = np.linalg.qr(crandn(rng, n, k))
+    perm = rng.permutation(k)
+    ph = np.exp(1j * rng.uniform(0, 2 * np.pi, k))
+    Xn = X[:, perm] * ph
+    inv = np.argsort(perm)
+    got, cost, nout = pieces.reindex(X, Xn, B, np.arange(k), np.arange(k)[perm])
+    assert np.array_equal(got, inv)
+    assert abs(cost) < 1e-12 and nout == 0
+    c = pieces.overlap_cosines(X, Xn, B)
+    assert np.allclose(c[np.arange(k), got], 1.0, atol=1e-12)
+
+
+def test_reindex_optimal_against_brute_force():
+    """The assignment equals the optimum over all permutations (tiny k), with no window and
+    with an energy window that forbids the unrestricted optimum: the new vectors are a
+    shuffled, perturbed copy of the old, while the new eigenvalues stay in place, so the
+    window admits only the pairs i -> i."""
+    import itertools
+    from oracle import pieces
+    rng = np.random.default_rng(4)
+    n, k = 30, 5
+    B = rand_hpd(rng, n, cond=10.0)
+    Xo = crandn(rng, n, k)
+    sh = np.array([1, 2, 3, 4, 0])
+    Xn = Xo[:, sh] + 0.6 * crandn(rng, n, k)
+    lo = np.array([0.0, 0.2, 0.4, 0.6, 0.8])
+    ln = lo + 0.01
+    c = pieces.overlap_cosines(Xo, Xn, B)
+    perms = {}
+    for window in (np.inf, 0.05):
+        far = np.abs(lo[:, None] - ln[None, :]) > window
+        # lexicographic: fewest pairs outside the window, then the least cost inside it
+        best = min((sum(far[i, p[i]] for i in range(k)),
+                    sum(0.0 if far[i, p[i]] else 1 - c[i, p[i]] for i in range(k)))
+                   for p in itertools.permutations(range(k)))
+        perm, cost, nout = pieces.reindex(Xo, Xn, B, lo, ln, window)
+        assert nout == best[0] == 0
+        assert abs(cost - best[1]) <= 1e-12 * max(1.0, best[1])
+        assert sorted(perm) == list(range(k))
+        perms[window] = perm
+    assert np.array_equal(perms[np.inf], np.argsort(sh))
+    assert np.array_equal(perms[0.05], np.arange(k))
+
+
+def test_overlap_cosines_known_angles():
+    """Vectors at known angles in the B inner product: with B = L L^H, y = L^-H e, the
+    cosine of y_old = L^-H e_1 and y_new = L^-H (cos phi e_1 + sin phi e_2) is cos phi
+    whatever the scaling of either vector; using B the wrong way (B^-1, B^T on complex data,
+    or no B) gives another value."""
+    from oracle import pieces
+    rng = np.random.default_rng(5)
+    n = 12
+    B = rand_hpd(rng, n, cond=50.0)
+    L = np.linalg.cholesky(B)
+    Linv_h = np.linalg.inv(L).conj().T
+    phis = np.array([0.0, 0.3, 1.1, np.pi / 2])
+    E = np.zeros((n, 4), dtype=complex)
+    E[0] = 1.0
+    Xo = Linv_h @ E * 2.5
+    F = np.zeros((n, 4), dtype=complex)
+    F[0] = np.cos(phis)
+    F[1] = np.sin(phis) * np.exp(0.7j)
+    Xn = Linv_h @ F * 0.3j
+    c = pieces.overlap_cosines(Xo, Xn, B)
+    assert np.allclose(np.diag(c), np.abs(np.cos(phis)), atol=1e-12)
+    th = pieces.deviation_angles(Xo, Xn, B)
+    assert np.allclose(th[:3], phis[:3] / (np.pi / 2), atol=1e-7)
+    assert not np.allclose(np.diag(pieces.overlap_cosines(Xo, Xn, np.eye(n))), np.abs(np.cos(phis)), atol=1e-3)
