@@ -80,7 +80,8 @@ typedef struct {
   int reduce_slices;    /* 0: the n^3 products of the reduction to standard form run on the */
                         /* FP64 pipe. 1..8: they are emulated on the tensor cores with that */
                         /* many 7-bit digits per entry (Ozaki scheme, exact digit products; */
-                        /* 8 digits keep FP64-class accuracy), see gevp_zgemm_emulated      */
+                        /* 8 digits keep FP64-class accuracy), see gevp_zgemm_emulated.    */
+                        /* gevp_solve_batched emulates its reduction one k-point at a time.  */
 } gevp_opts;
 
 /* Per-problem counters and CUDA-event phase times (milliseconds). */
@@ -102,7 +103,7 @@ typedef struct {
 
 /* Fills *o with the defaults: FP64 filter, tol 1e-10, max_outer 60, degrees 4..48,
  * nex 0 (callers set it), seed 10074400, b_fixed 0, cold_start 0, lanczos_steps 32,
- * refine_iters 3, keep_all_X 0. */
+ * refine_iters 3, keep_all_X 0, refresh_window 0, reduce_slices 8. */
 void gevp_default_opts(gevp_opts* o);
 
 /* Creates a handle on CUDA device `device` bound to `stream` (a cudaStream_t; NULL =
@@ -300,21 +301,23 @@ gevp_status gevp_deviation_angles(gevp_handle h, int64_t n, int k_old, int k_new
 gevp_status gevp_assign_min_cost(int ko, int kn, const double* cost, int64_t* perm);
 
 /* FP64 complex product emulated on the tensor cores (Ozaki scheme; beyond the paper, which
- * keeps every step in FP64): D (M x N) = A B^H with A M x K and B N x K, device row-major
- * complex128 (ld lda, ldb, ldd). Each row of A and of B is scaled by a power of two so its
+ * keeps every step in FP64): D (M x N) = op(A) op(B), op(X) = X (op 0) or X^H (op 1):
+ * A is M x K (opA 0, lda >= K) or K x M (opA 1, lda >= M), B is K x N (opB 0, ldb >= N) or
+ * N x K (opB 1, ldb >= K); device row-major complex128. Each row of op(A) and each column
+ * of op(B) is scaled by a power of two so its
  * largest real or imaginary part lies in [1/4, 1/2), rounded to `slices` signed 7-bit
  * digits (1..8) and the digit planes are multiplied exactly in BF16 with FP32
  * accumulation (units of at most 2048 complex terms); pairs of digits whose weights sum
  * past the last digit are left out; the exact integer sums are combined in FP64.
- *   Error of entry (i, j): at most about 2K (slices + 3) 2^(-7 slices + 2) max_k|A_ik|
- *   max_k|B_jk| (FP64's own bound is K u sum_k |A_ik||B_jk|, u = 2^-53); with 8 digits
- *   the two are of the same order.
+ *   Error of entry (i, j): at most about 2K (slices + 3) 2^(-7 slices + 2) max_k|op(A)_ik|
+ *   max_k|op(B)_kj| (FP64's own bound is K u sum_k |op(A)_ik||op(B)_kj|, u = 2^-53); with
+ *   8 digits the two are of the same order.
  *   K <= 30720 (else GEVP_ERR_UNSUPPORTED); GEVP_ERR_INVALID_VALUE on NaN or Inf in A or B.
  *   Device scratch of slices * (4 M_pad + 6 N_pad) * K_pad bytes (M_pad, N_pad: M, N
  *   rounded up to 128; K_pad: K rounded up to 64) is kept by the handle. Needs an sm_103 device (GEVP_ERR_UNSUPPORTED otherwise).
  *   Returns after the work is complete. */
-gevp_status gevp_zgemm_emulated(gevp_handle h, int M, int N, int K, const void* A, int64_t lda, const void* B,
-                                int64_t ldb, void* D, int64_t ldd, int slices);
+gevp_status gevp_zgemm_emulated(gevp_handle h, int opA, int opB, int M, int N, int K, const void* A, int64_t lda,
+                                const void* B, int64_t ldb, void* D, int64_t ldd, int slices);
 
 /* gevp_reduce with the two n^3 products of the reduction (T = L^-1 tril(A) with the
  * diagonal halved, M = T L^-H, C = M + M^H) emulated as in gevp_zgemm_emulated with

@@ -119,6 +119,15 @@ struct BatchPlan {
   float t_step = 0.f, t_rest = 0.f;   // ms per filter step (whole batch), ms per round besides the filter
   std::vector<int> bucket;
   int cap_bucket[kBuckets];
+  // emulated reduction: digit forms of every k-point's L^-1 (left operand) and L^-H (right
+  // operand), made once per call, plus one k-point's worth of scratch for tril(A) and T
+  int oz_S = 0;
+  char* oz_mem = nullptr;
+  size_t oz_bytes = 0;
+  std::vector<OzOperand> ozLA, ozLB;
+  OzOperand ozAB, ozTA;
+  char* oz_scratch = nullptr;
+  int* oz_flags = nullptr;   // device: [0] kernel error code, [1] non-finite entry
   std::vector<cudaEvent_t> ev;
 };
 
@@ -127,6 +136,7 @@ void batch_release(BatchPlan* P) {
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->arena) cudaFree(P->arena);
+  if (P->oz_mem) cudaFree(P->oz_mem);
   if (P->hD) cudaFreeHost(P->hD);
   for (auto e : P->ev) cudaEventDestroy(e);
   delete P;
@@ -719,6 +729,39 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
       ctx_set_error(h, buf);
       return GEVP_ERR_NOT_HPD;
     }
+  // digit forms of L^-1 for the emulated reduction (o.reduce_slices digits per entry)
+  P->oz_S = (o.reduce_slices > 0 && oz_supported() && P->nmax <= 30720) ? o.reduce_slices : 0;
+  if (P->oz_S > 0) {
+    const int S = P->oz_S;
+    size_t need = 256, scratch = 0;
+    for (int k = 0; k < np; ++k) {
+      const int nk_ = (int)n[k];
+      need += oz_operand_bytes(nk_, nk_, S, 2) + oz_operand_bytes(nk_, nk_, S, 3);
+      scratch = std::max(scratch, oz_operand_bytes(nk_, nk_, S, 2) + oz_operand_bytes(nk_, nk_, S, 3));
+    }
+    need += scratch;
+    if (need > P->oz_bytes) {
+      if (P->oz_mem) cudaFree(P->oz_mem);
+      P->oz_mem = nullptr;
+      P->oz_bytes = 0;
+      BCK(cudaMalloc(&P->oz_mem, need));
+      P->oz_bytes = need;
+    }
+    P->oz_flags = (int*)P->oz_mem;
+    BCK(cudaMemsetAsync(P->oz_flags, 0, 2 * sizeof(int), s));
+    char* q = P->oz_mem + 256;
+    P->ozLA.assign(np, OzOperand{});
+    P->ozLB.assign(np, OzOperand{});
+    for (int k = 0; k < np; ++k) {
+      const BDesc& d = P->hD[k];
+      const int nk_ = (int)n[k];
+      BCK(oz_split(P->ozLA[k], q, nk_, nk_, d.Linv, n[k], 0, 2, S, 2, P->oz_flags + 1, s));
+      q += oz_operand_bytes(nk_, nk_, S, 2);
+      BCK(oz_split(P->ozLB[k], q, nk_, nk_, d.Linv, n[k], 1, 2, S, 3, P->oz_flags + 1, s));
+      q += oz_operand_bytes(nk_, nk_, S, 3);
+    }
+    P->oz_scratch = q;
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, evt(P, EV_T0), evt(P, EV_CHOL));
   bs->ms_chol += ms;
@@ -776,8 +819,22 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
     BCK(cudaEventRecord(evt(P, EV_T0), s));
     bk_step_reset(P->dD, np, o.tol, tc ? 0 : 1, s);
     // ---- reduction C = L^-1 A L^-H for every k-point
-    launch(P, P->c_red1, s, tune);
-    launch(P, P->c_red2, s, tune);
+    if (P->oz_S > 0) {
+      // emulated: T = L^-1 tril_half(A), M = T L^-H per k-point (each product fills the GPU)
+      for (int k = 0; k < np; ++k) {
+        const BDesc& d = P->hD[k];
+        const int nk_ = (int)n[k], S = P->oz_S;
+        char* base = P->oz_scratch;
+        BCK(oz_split(P->ozAB, base, nk_, nk_, d.A, d.lda, 1, 1, S, 3, P->oz_flags + 1, s));
+        BCK(oz_gemm(P->ozLA[k], P->ozAB, 1, 1, d.T, n[k], P->oz_flags, s));
+        BCK(oz_split(P->ozTA, base + oz_operand_bytes(nk_, nk_, S, 3), nk_, nk_, d.T, n[k], 0, 2, S, 2,
+                     P->oz_flags + 1, s));
+        BCK(oz_gemm(P->ozTA, P->ozLB[k], 1, 2, d.C, n[k], P->oz_flags, s));
+      }
+    } else {
+      launch(P, P->c_red1, s, tune);
+      launch(P, P->c_red2, s, tune);
+    }
     bk_herm_sum(P->dD, np, P->nmax, s);
     BCK(cudaEventRecord(evt(P, EV_RED), s));
     // ---- bounds of C (and ||A||_2)
@@ -941,6 +998,14 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
   }
   BCK(cudaEventRecord(evt(P, EV_END), s));
   BCK(cudaStreamSynchronize(s));
+  if (P->oz_S > 0) {
+    int f[2] = {0, 0};
+    BCK(cudaMemcpy(f, P->oz_flags, sizeof f, cudaMemcpyDeviceToHost));
+    if (f[0]) {
+      ctx_set_error(h, "a bounded wait of the emulated FP64 product ran out");
+      return GEVP_ERR_TIMEOUT;
+    }
+  }
   bs->converged = overall == GEVP_OK ? 1 : 0;
   bs->max_resid = maxres;
   for (int c = 0; c < 8; ++c) bs->tile[c] = 0;

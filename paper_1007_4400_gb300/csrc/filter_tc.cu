@@ -428,7 +428,10 @@ bool tc_filter_supported() {
   return major == 10 && minor == 3 && get_encode() != nullptr;
 }
 
-cudaError_t filter_tc_reserve(FilterTC** pf, int64_t n, int m) {
+// Zero fill on stream s: a plain cudaMemset runs on the legacy default stream, which is
+// not ordered with the library's non-blocking streams, and could land after the planes
+// that s writes next.
+cudaError_t filter_tc_reserve(FilterTC** pf, int64_t n, int m, cudaStream_t s) {
   if (!*pf) *pf = new FilterTC();
   FilterTC* f = *pf;
   int n_pad = pad_to((int)n, TM);
@@ -448,7 +451,8 @@ cudaError_t filter_tc_reserve(FilterTC** pf, int64_t n, int m) {
                  1024;
   cudaError_t e = cudaMalloc(&f->arena, bytes);
   if (e != cudaSuccess) { f->arena = nullptr; f->n_pad = f->ncols_pad = 0; return e; }
-  cudaMemset(f->arena, 0, bytes);
+  e = cudaMemsetAsync(f->arena, 0, bytes, s);
+  if (e != cudaSuccess) return e;
   char* p = (char*)f->arena;
   f->Cp = (__nv_bfloat16*)p; p += al((size_t)MAXSPLIT * 3 * np2 * 2);
   f->Yp = (__nv_bfloat16*)p; p += al((size_t)MAXSPLIT * 3 * nc * 2);

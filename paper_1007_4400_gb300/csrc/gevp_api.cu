@@ -65,6 +65,12 @@ struct gevp_ctx {
   char* ozmem[2] = {nullptr, nullptr};      // [0] L^-1 operands + main-stream scratch, [1] side stream
   size_t ozmem_bytes[2] = {0, 0};
   gevp::OzOperand ozLA, ozLB, ozAB[2], ozTA[2];
+  // solver products on the main stream: C (rows, per problem), A (rows, per final check),
+  // B (rows, kept while the factorisation is), the block (columns, per product)
+  gevp::OzOperand ozC, ozA, ozB, ozQ;
+  const void* ozC_src = nullptr;            // the C whose digits ozC holds (null: none)
+  const void* ozB_src = nullptr;            // the B whose digits ozB holds, for chol_gen ozB_gen
+  int64_t ozB_gen = -1;
   int64_t oz_l_gen = -1;                    // chol_gen the L^-1 operands were split from
   int oz_l_S = 0;
   int64_t chol_gen = 0;                     // incremented by every factorisation of B
@@ -341,11 +347,39 @@ gevp_status oz_reserve(gevp_ctx* h, int side, size_t need) {
   if (h->ozmem[side]) cudaFree(h->ozmem[side]);
   h->ozmem[side] = nullptr;
   h->ozmem_bytes[side] = 0;
-  if (side == 0) h->oz_l_gen = -1;
+  if (side == 0) {
+    h->oz_l_gen = -1;
+    h->ozC_src = nullptr;
+    h->ozB_src = nullptr;
+  }
   void* p = nullptr;
   CK(cudaMalloc(&p, need));
   h->ozmem[side] = (char*)p;
   h->ozmem_bytes[side] = need;
+  return GEVP_OK;
+}
+
+// Main-stream digit scratch: [L^-1 rows | L^-H columns | reduction: tril(A) | T | A | B]
+// (the solver's C digits reuse the T region and the block's digits the tril(A) region:
+// the reduction of a problem is finished before its solve starts, on the same stream)
+size_t oz_main_bytes(int64_t n, int S) {
+  const size_t bA = gevp::oz_operand_bytes((int)n, (int)n, S, 2), bB = gevp::oz_operand_bytes((int)n, (int)n, S, 3);
+  return 4 * bA + 2 * bB;
+}
+char* oz_region(gevp_ctx* h, int64_t n, int which) {   // 0 L^-1, 1 L^-H, 2 tril(A)/block, 3 T/C, 4 A, 5 B
+  const int S = h->oz_slices;
+  const size_t bA = gevp::oz_operand_bytes((int)n, (int)n, S, 2), bB = gevp::oz_operand_bytes((int)n, (int)n, S, 3);
+  const size_t off[6] = {0, bA, bA + bB, bA + 2 * bB, 2 * bA + 2 * bB, 3 * bA + 2 * bB};
+  return h->ozmem[0] + off[which];
+}
+
+// D (n x ncols, ld ldd) = M X with M one of the cached square operands (ozC, ozA, ozB) and
+// X the n x ncols block (ld ldx), emulated on the main stream
+gevp_status oz_times_block(gevp_ctx* h, const gevp::OzOperand& M, int64_t n, int ncols, const double2* X,
+                           int64_t ldx, double2* D, int64_t ldd) {
+  CK(gevp::oz_split(h->ozQ, oz_region(h, n, 2), ncols, (int)n, X, ldx, 0, 0, h->oz_slices, 3, h->ozflags + 1,
+                    h->stream, true));
+  CK(gevp::oz_gemm(M, h->ozQ, 0, 0, D, ldd, h->ozflags, h->stream));
   return GEVP_OK;
 }
 
@@ -354,7 +388,7 @@ gevp_status reduce_emulated(gevp_ctx* h, int side, int64_t n, const double2* A, 
   const int S = h->oz_slices;
   const int nn = (int)n;
   const size_t bA = gevp::oz_operand_bytes(nn, nn, S, 2), bB = gevp::oz_operand_bytes(nn, nn, S, 3);
-  TRY(oz_reserve(h, side, (side == 0 ? bA + bB : 0) + bA + bB));
+  TRY(oz_reserve(h, side, side == 0 ? oz_main_bytes(n, S) : bA + bB));
   char* mem = h->ozmem[side];
   if (side == 0 && (h->oz_l_gen != h->chol_gen || h->oz_l_S != S)) {
     // L^-1 as the left operand (rows, lower) and L^-H as the right one (rows of L^-1, conjugated)
@@ -521,8 +555,12 @@ gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const doubl
                           int refine, gevp_stats* st) {
   const int64_t ld = h->cap_m;
   double2* Qa = h->Q + nlock;
-  ZgemmArgs w = zg((int)n, ma, (int)n, C, ldc, 0, Qa, ld, 0, h->Wt, ld);
-  zgemm(w, h->split, h->split_elems, h->stream);
+  if (h->oz_slices > 0 && h->ozC_src == (const void*)C) {
+    TRY(oz_times_block(h, h->ozC, n, ma, Qa, ld, h->Wt, ld));
+  } else {
+    ZgemmArgs w = zg((int)n, ma, (int)n, C, ldc, 0, Qa, ld, 0, h->Wt, ld);
+    zgemm(w, h->split, h->split_elems, h->stream);
+  }
   ZgemmArgs g = zg(ma, ma, (int)n, Qa, ld, 1, h->Wt, ld, 0, h->G, ma);
   zgemm(g, h->split, h->split_elems, h->stream);
   heev_small(ma, h->G, ma, h->theta + nlock, h->Zs, ma, h->hw, refine, h->stream);
@@ -659,8 +697,17 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   int prec = o.filter_prec;
   const int nsplit = (prec == GEVP_PREC_FP32) ? 3 : 1;
   if (prec != GEVP_PREC_FP64 && !tc_ready) {
-    CK(filter_tc_reserve(&h->tc, n, m));
+    CK(filter_tc_reserve(&h->tc, n, m, h->stream));
     CK(filter_tc_set_matrix(h->tc, n, h->C, n, nsplit, h->stream));
+  }
+  // emulated products: the digits of C for every W = C Q of this problem
+  const bool oz = h->oz_slices > 0;
+  bool oz_a_ready = false;
+  if (oz) {
+    TRY(oz_reserve(h, 0, oz_main_bytes(n, h->oz_slices)));
+    CK(gevp::oz_split(h->ozC, oz_region(h, n, 3), (int)n, (int)n, h->C, n, 0, 0, h->oz_slices, 2, h->ozflags + 1,
+                      h->stream));
+    h->ozC_src = h->C;
   }
   tm.mark(PH_BOUNDS);
   if (!warm) {
@@ -690,10 +737,29 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
       ZgemmArgs x = zg((int)n, nev, (int)n, h->Linv, n, 1, h->Q, ld, 0, h->Xf, ld);
       x.triA = 2;
       zgemm(x, h->split, h->split_elems, h->stream);
-      ZgemmArgs ax = zg((int)n, nev, (int)n, A, lda, 0, h->Xf, ld, 0, h->Y1, ld);
-      zgemm(ax, h->split, h->split_elems, h->stream);
-      ZgemmArgs bx = zg((int)n, nev, (int)n, B, ldb, 0, h->Xf, ld, 0, h->Y2, ld);
-      zgemm(bx, h->split, h->split_elems, h->stream);
+      if (oz) {
+        // A X and B X emulated: A's digits once per problem, B's while it stays factorised
+        if (!oz_a_ready) {
+          CK(gevp::oz_split(h->ozA, oz_region(h, n, 4), (int)n, (int)n, A, lda, 0, 0, h->oz_slices, 2,
+                            h->ozflags + 1, h->stream));
+          oz_a_ready = true;
+        }
+        if (h->ozB_src != (const void*)B || h->ozB_gen != h->chol_gen) {
+          CK(gevp::oz_split(h->ozB, oz_region(h, n, 5), (int)n, (int)n, B, ldb, 0, 0, h->oz_slices, 2,
+                            h->ozflags + 1, h->stream));
+          h->ozB_src = B;
+          h->ozB_gen = h->chol_gen;
+        }
+        CK(gevp::oz_split(h->ozQ, oz_region(h, n, 2), nev, (int)n, h->Xf, ld, 0, 0, h->oz_slices, 3, h->ozflags + 1,
+                          h->stream, true));
+        CK(gevp::oz_gemm(h->ozA, h->ozQ, 0, 0, h->Y1, ld, h->ozflags, h->stream));
+        CK(gevp::oz_gemm(h->ozB, h->ozQ, 0, 0, h->Y2, ld, h->ozflags, h->stream));
+      } else {
+        ZgemmArgs ax = zg((int)n, nev, (int)n, A, lda, 0, h->Xf, ld, 0, h->Y1, ld);
+        zgemm(ax, h->split, h->split_elems, h->stream);
+        ZgemmArgs bx = zg((int)n, nev, (int)n, B, ldb, 0, h->Xf, ld, 0, h->Y2, ld);
+        zgemm(bx, h->split, h->split_elems, h->stream);
+      }
       // Y1/Y2 share ld; final_check wants one ld for X, AX, BX
       final_check(n, nev, h->Xf, h->Y1, h->Y2, ld, h->lam, h->resf, S.normA, h->partial, h->stream);
       if (st) st->flops_fp64 += 8.0 * (double)n * n * nev * 2.5;
@@ -804,6 +870,7 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   CK(cudaMemcpyAsync(res_out, h->resf, nev * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (X_out) zcopy2d(n, nev, h->Xf, ld, X_out, ldx, h->stream);
   if (st) st->converged = converged ? 1 : 0;
+  h->ozC_src = nullptr;   // C's digits are this problem's only
   return converged ? GEVP_OK : GEVP_ERR_NO_CONVERGENCE;
 }
 
@@ -827,7 +894,7 @@ gevp_status prefetch_problem(gevp_ctx* h, int64_t n, int m, const double2* A, in
   lanczos_bounds(n, h->M32b, n, o.lanczos_steps, 0, o.seed + 104729ull * idx + 1, h->lw2, h->bounds2 + 8, h->side);
   CK(cudaMemcpyAsync(h->hb2, h->bounds2, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->side));
   if (o.filter_prec != GEVP_PREC_FP64) {
-    CK(filter_tc_reserve(&h->tc2, n, m));
+    CK(filter_tc_reserve(&h->tc2, n, m, h->side));
     CK(filter_tc_set_matrix(h->tc2, n, h->C2, n, o.filter_prec == GEVP_PREC_FP32 ? 3 : 1, h->side));
   }
   CK(cudaEventRecord(h->ev_side, h->side));
@@ -883,6 +950,9 @@ void gevp_default_opts(gevp_opts* o) {
   o->lanczos_steps = 32;
   o->refine_iters = 3;
   o->keep_all_X = 0;
+  // the reduction's n^3 products emulated with 8 digits: FP64-class accuracy, about 17x
+  // the FP64 pipe's rate at n = 2048
+  o->reduce_slices = 8;
 }
 
 const char* gevp_status_string(gevp_status s) {
@@ -1204,7 +1274,7 @@ gevp_status gevp_chebyshev_filter(gevp_handle h, int64_t n, const void* C, int64
   if (prec != GEVP_PREC_FP64) {
     if (!tc_filter_supported()) return GEVP_ERR_UNSUPPORTED;
     const int nsplit = (prec == GEVP_PREC_FP32) ? 3 : 1;
-    CK(filter_tc_reserve(&h->tc, n, m));
+    CK(filter_tc_reserve(&h->tc, n, m, h->stream));
     CK(filter_tc_set_matrix(h->tc, n, (const double2*)C, ldc, nsplit, h->stream));
     int err = 0;
     CK(filter_tc_apply(h->tc, n, m, (const double2*)Y, ldy, (double2*)Y, ldy, degree, lo, hi, s, nsplit, &err,
@@ -1228,7 +1298,7 @@ gevp_status gevp_matmul_tc(gevp_handle h, int64_t n, int m, const void* C, int64
   if (!C || !Y || !D || bad_ld(ldc, n) || bad_ld(ldy, m) || bad_ld(ldd, m)) return GEVP_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   if (!tc_filter_supported()) return GEVP_ERR_UNSUPPORTED;
-  CK(filter_tc_reserve(&h->tc, n, m));
+  CK(filter_tc_reserve(&h->tc, n, m, h->stream));
   CK(filter_tc_set_matrix(h->tc, n, (const double2*)C, ldc, 1, h->stream));
   int err = 0;
   CK(filter_tc_product(h->tc, n, m, (const double2*)Y, ldy, (double2*)D, ldd, 1, &err, h->stream));
@@ -1479,12 +1549,13 @@ gevp_status gevp_assign_min_cost(int ko, int kn, const double* cost, int64_t* pe
   return GEVP_OK;
 }
 
-gevp_status gevp_zgemm_emulated(gevp_handle h, int M, int N, int K, const void* A, int64_t lda, const void* B,
-                                int64_t ldb, void* D, int64_t ldd, int slices) {
+gevp_status gevp_zgemm_emulated(gevp_handle h, int opA, int opB, int M, int N, int K, const void* A, int64_t lda,
+                                const void* B, int64_t ldb, void* D, int64_t ldd, int slices) {
   if (!h || M < 0 || N < 0 || K < 0 || slices < 1 || slices > gevp::kOzSlicesMax) return GEVP_ERR_INVALID_ARG;
+  if ((opA != 0 && opA != 1) || (opB != 0 && opB != 1)) return GEVP_ERR_INVALID_ARG;
   if (M == 0 || N == 0) return GEVP_OK;
   if (!D || bad_ld(ldd, N)) return GEVP_ERR_INVALID_ARG;
-  if (K > 0 && (!A || !B || bad_ld(lda, K) || bad_ld(ldb, K))) return GEVP_ERR_INVALID_ARG;
+  if (K > 0 && (!A || !B || bad_ld(lda, opA ? M : K) || bad_ld(ldb, opB ? K : N))) return GEVP_ERR_INVALID_ARG;
   if (K > 30720) {
     h->err = "emulated product: K above 30720";
     return GEVP_ERR_UNSUPPORTED;
@@ -1502,9 +1573,12 @@ gevp_status gevp_zgemm_emulated(gevp_handle h, int M, int N, int K, const void* 
   const size_t bA = gevp::oz_operand_bytes(M, K, slices, 2), bB = gevp::oz_operand_bytes(N, K, slices, 3);
   TRY(oz_reserve(h, 1, bA + bB));
   gevp::OzOperand a, b;
-  CK(gevp::oz_split(a, h->ozmem[1], M, K, (const double2*)A, lda, 0, 0, slices, 2, h->ozflags + 1, h->stream));
-  CK(gevp::oz_split(b, h->ozmem[1] + bA, N, K, (const double2*)B, ldb, 1, 0, slices, 3, h->ozflags + 1,
-                    h->stream));
+  // rows of op(A): rows of A, or conjugated columns; columns of op(B): columns of B, or
+  // conjugated rows
+  CK(gevp::oz_split(a, h->ozmem[1], M, K, (const double2*)A, lda, opA, 0, slices, 2, h->ozflags + 1, h->stream,
+                    opA == 1));
+  CK(gevp::oz_split(b, h->ozmem[1] + bA, N, K, (const double2*)B, ldb, opB, 0, slices, 3, h->ozflags + 1,
+                    h->stream, opB == 0));
   CK(gevp::oz_gemm(a, b, 0, 0, (double2*)D, ldd, h->ozflags, h->stream));
   return oz_check(h);
 }

@@ -156,7 +156,7 @@ void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const
 // ---------------------------------------------------------------- low-precision filter (tcgen05)
 struct FilterTC;   // opaque, owned by the handle
 bool tc_filter_supported();
-cudaError_t filter_tc_reserve(FilterTC** f, int64_t n, int m);
+cudaError_t filter_tc_reserve(FilterTC** f, int64_t n, int m, cudaStream_t s);
 void filter_tc_release(FilterTC* f);
 // nsplit: BF16 pieces per operand (1 = BF16 filter, 3 = FP32-class, see filter_tc.cu)
 cudaError_t filter_tc_set_matrix(FilterTC* f, int64_t n, const double2* C, int64_t ldc, int nsplit, cudaStream_t s);
@@ -272,10 +272,11 @@ struct OzOperand {
 };
 size_t oz_operand_bytes(int rows, int K, int S, int npl);
 bool oz_supported();
-// rows of X (conj: conjugated; mask 1: k >= r with the diagonal halved, 2: k <= r) into
-// digit form in `mem` (oz_operand_bytes); *bad = 1 on a non-finite entry
+// rows of X (cols = false; X is rows x K) or its columns (cols = true; X is K x rows) as
+// operand rows, conjugated if conj, mask 1: k >= r with the diagonal halved, 2: k <= r,
+// 3: k >= r; into digit form in `mem` (oz_operand_bytes); *bad = 1 on a non-finite entry
 cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
-                     int S, int npl, int* bad, cudaStream_t s);
+                     int S, int npl, int* bad, cudaStream_t s, bool cols = false);
 // D (A.rows x B.rows) = op(A) op(B); triA 1: op(A) lower; triB 1: op(B) lower, 2: upper
 cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
                     cudaStream_t s);

@@ -94,10 +94,11 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // Task e of one rotation step. The pairs of a round are disjoint, so G <- U^H G U splits
 // into independent 2 x 2 blocks G[{p,q},{r,s}] <- U_a^H G[{p,q},{r,s}] U_b (tasks
 // e < npairs^2, a = row pair, b = column pair), and Z <- Z U into independent row pieces
-// (tasks after those). Every element is read and written once per step.
+// (tasks after those). Every element of G is read from G and written to Gout once per
+// step (Gout = G in place, or the other buffer of a ping-pong pair).
 template <bool L2 = false>
-__device__ __forceinline__ void jacobi_apply(float2* G, float2* Z, int m, int npairs, int e, const float4* U,
-                                             const int (*PQ)[2]) {
+__device__ __forceinline__ void jacobi_apply(const float2* G, float2* Gout, float2* Z, int m, int npairs, int e,
+                                             const float4* U, const int (*PQ)[2]) {
   if (e < npairs * npairs) {
     const int a = e / npairs, b = e % npairs;
     const int p = PQ[a][0], q = PQ[a][1], r = PQ[b][0], s = PQ[b][1];
@@ -144,10 +145,10 @@ __device__ __forceinline__ void jacobi_apply(float2* G, float2* Z, int m, int np
       gpr.y = 0.f;
       gqs.y = 0.f;
     }
-    G[p * m + r] = gpr;
-    if (sv) G[p * m + s] = gps;
-    if (qv) G[q * m + r] = gqr;
-    if (qv && sv) G[q * m + s] = gqs;
+    Gout[p * m + r] = gpr;
+    if (sv) Gout[p * m + s] = gps;
+    if (qv) Gout[q * m + r] = gqr;
+    if (qv && sv) Gout[q * m + s] = gqs;
   } else {
     const int t = e - npairs * npairs;
     const int i = t / npairs, b = t % npairs;
@@ -202,7 +203,7 @@ __device__ void jacobi32_body(int m, float2* Gg, float2* Z, float* w, int* perm,
     for (int step = 0; step < np - 1; ++step) {
       for (int k = tid; k < npairs; k += JT) jacobi_pair_params(G, m, np, step, k, U, PQ);
       __syncthreads();
-      for (int e = tid; e < npairs * npairs + m * npairs; e += JT) jacobi_apply(G, Z, m, npairs, e, U, PQ);
+      for (int e = tid; e < npairs * npairs + m * npairs; e += JT) jacobi_apply(G, G, Z, m, npairs, e, U, PQ);
       __syncthreads();
     }
   }
@@ -224,9 +225,12 @@ constexpr int kJacobiSmemMax = 160;   // largest m whose G (m * m FP32 complex) 
 // Multi-CTA variant for orders above the one-CTA shared-memory size: the same rounds, each
 // CTA computing every rotation of a round (redundantly, from G in global memory) and
 // applying its share of the 2 x 2 block and Z tasks, with one grid barrier per round
-// (cooperative launch: all CTAs are resident). red: 2 + max_sweeps floats, zero on entry.
-__global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, float2* Z, float* w, int* perm,
-                                                           int max_sweeps, float* red_g) {
+// (cooperative launch: all CTAs are resident). The rounds alternate between G and Gb
+// (m x m each): a round reads one and writes the other, so a CTA still computing the
+// round's rotations never sees entries another CTA has already rotated. red: 2 +
+// max_sweeps floats, zero on entry. G and Gb are both destroyed.
+__global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, float2* Gb, float2* Z, float* w,
+                                                           int* perm, int max_sweeps, float* red_g) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ float4 U[512];
@@ -245,11 +249,13 @@ __global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, flo
   const float fro2 = __ldcg(&red_g[0]);
   const float tol2 = 1e-16f * fro2;
   float off_prev = 3.0e38f;
+  float2* Gc = G;    // the current matrix; rounds write the other buffer
+  float2* Gn = Gb;
   for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
     float off = 0.f;
     for (int e = gtid; e < m * m; e += gsz) {
       int i = e / m, j = e % m;
-      if (i != j) { float2 g = __ldcg(G + e); off += g.x * g.x + g.y * g.y; }
+      if (i != j) { float2 g = __ldcg(Gc + e); off += g.x * g.x + g.y * g.y; }
     }
     off = block_sum(off, red);
     if (tid == 0) atomicAdd(&red_g[1 + sweep], off);
@@ -258,18 +264,22 @@ __global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, flo
     if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
     off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
-      for (int k = tid; k < npairs; k += JT) jacobi_pair_params<true>(G, m, np, step, k, U, PQ);
+      for (int k = tid; k < npairs; k += JT) jacobi_pair_params<true>(Gc, m, np, step, k, U, PQ);
       __syncthreads();
-      for (int e = gtid; e < npairs * npairs + m * npairs; e += gsz) jacobi_apply<true>(G, Z, m, npairs, e, U, PQ);
+      for (int e = gtid; e < npairs * npairs + m * npairs; e += gsz)
+        jacobi_apply<true>(Gc, Gn, Z, m, npairs, e, U, PQ);
       grid.sync();
+      float2* t = Gc;
+      Gc = Gn;
+      Gn = t;
     }
   }
   if (blockIdx.x != 0) return;
   for (int i = tid; i < m; i += JT) {
-    float wi = __ldcg(G + i * m + i).x;
+    float wi = __ldcg(Gc + i * m + i).x;
     int r = 0;
     for (int j = 0; j < m; ++j) {
-      float wj = __ldcg(G + j * m + j).x;
+      float wj = __ldcg(Gc + j * m + j).x;
       r += (wj < wi) || (wj == wi && j < i);
     }
     perm[r] = i;
@@ -515,7 +525,8 @@ size_t heev_ws_bytes(int m, size_t split_elems) {
 
 // Cooperative multi-CTA Jacobi for large m; false if it cannot be launched (then the
 // caller runs the one-CTA kernel).
-bool jacobi32_coop(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, float* red, cudaStream_t s) {
+bool jacobi32_coop(int m, float2* G, float2* Gb, float2* Z, float* w, int* perm, int max_sweeps, float* red,
+                   cudaStream_t s) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -529,7 +540,7 @@ bool jacobi32_coop(int m, float2* G, float2* Z, float* w, int* perm, int max_swe
   grid = std::max(grid, 1);
   if (max_sweeps > 62) max_sweeps = 62;
   if (cudaMemsetAsync(red, 0, 64 * sizeof(float), s) != cudaSuccess) return false;
-  void* args[] = {&m, &G, &Z, &w, &perm, &max_sweeps, &red};
+  void* args[] = {&m, &G, &Gb, &Z, &w, &perm, &max_sweeps, &red};
   if (cudaLaunchCooperativeKernel((const void*)jacobi32_coop_kernel, grid, JT, args, 0, s) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -566,7 +577,9 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   LAUNCH_NOTE(1);
   // large orders on all SMs (cooperative launch); otherwise, or if that launch is not
   // possible, one CTA
-  const bool coop = m > kJacobiSmemMax && jacobi32_coop(m, w.G32, w.Z32, w.w32, w.perm, 40, (float*)(w.scal + 16), s);
+  // (the FP64 scratch E, unused until the refinement, holds the second FP32 buffer)
+  const bool coop = m > kJacobiSmemMax && jacobi32_coop(m, w.G32, (float2*)w.E, w.Z32, w.w32, w.perm, 40,
+                                                        (float*)(w.scal + 16), s);
   if (!coop) {
     jacobi32_kernel<<<1, JT, jacobi_smem(m), s>>>(m, w.G32, w.Z32, w.w32, w.perm, 40);
     LAUNCH_NOTE(1);

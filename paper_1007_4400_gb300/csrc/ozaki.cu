@@ -256,20 +256,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   }
 }
 
-// Digits of one row (a row of op(A), or a column of op(B) read as a row of the stored
-// matrix): entry k of row r is X[r][k], conjugated if conj; mask 1 keeps k >= r with the
-// diagonal halved (a column of the lower triangle of a Hermitian matrix, tril(A) with its
-// diagonal split between A and A^H), mask 2 keeps k <= r. Writes the exponent of the row
-// and the S digits of the real part, the imaginary part and (npl = 3) the negated
-// imaginary part into planes [npl][S][rows_pad][k_pad]; rows and columns past the matrix
+// Digits of one operand row r (a row of op(A), or a column of op(B)), entries k < K. The
+// row is row r of the stored X (oz_split_rows_kernel) or its column r
+// (oz_split_cols_kernel), conjugated if conj; mask 1 keeps k >= r with the diagonal halved
+// (a column of the lower triangle of a Hermitian matrix, tril(A) with its diagonal split
+// between A and A^H), mask 2 keeps k <= r, mask 3 keeps k >= r. Writes the exponent of the
+// row and the S digits of the real part, the imaginary part and (npl = 3) the negated
+// imaginary part into planes [npl][S][rows_pad][k_pad]; rows and entries past the operand
 // are zero. A row with a non-finite entry sets *bad.
-__device__ __forceinline__ double2 oz_entry(const double2* X, int64_t ldx, int r, int k, int K, int conj, int mask) {
-  if (k >= K) return make_double2(0.0, 0.0);
-  if ((mask == 1 && k < r) || (mask == 2 && k > r)) return make_double2(0.0, 0.0);
-  double2 v = X[(int64_t)r * ldx + k];
+__device__ __forceinline__ double2 oz_masked(double2 v, int r, int k, int conj, int mask) {
+  if ((mask == 1 && k < r) || (mask == 2 && k > r) || (mask == 3 && k < r)) return make_double2(0.0, 0.0);
   if (conj) v.y = -v.y;
   if (mask == 1 && k == r) v = make_double2(0.5 * v.x, 0.5 * v.y);
   return v;
+}
+
+__device__ __forceinline__ double2 oz_entry(const double2* X, int64_t ldx, int r, int k, int K, int conj, int mask) {
+  if (k >= K) return make_double2(0.0, 0.0);
+  return oz_masked(X[(int64_t)r * ldx + k], r, k, conj, mask);
+}
+
+__device__ __forceinline__ bool oz_finite(double2 v) {
+  return fabs(v.x) <= 1.7976931348623157e308 && fabs(v.y) <= 1.7976931348623157e308;
 }
 
 __device__ __forceinline__ void oz_digits(double x, int shift, int S, __nv_bfloat16* out, size_t plane) {
@@ -292,9 +300,9 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, con
   if (r < rows)
     for (int k = threadIdx.x; k < K; k += 256) {
       const double2 v = oz_entry(X, ldx, r, k, K, conj, mask);
-      const double a = fmax(fabs(v.x), fabs(v.y));
-      if (!(a <= 1.7976931348623157e308)) nonfinite = true;   // NaN or Inf
-      else mx = fmax(mx, a);
+      // NaN or Inf (tested per part: fmax would drop a NaN)
+      if (!oz_finite(v)) nonfinite = true;
+      else mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
   if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -311,6 +319,59 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, con
   for (int k = threadIdx.x; k < k_pad; k += 256) {
     const double2 v = r < rows ? oz_entry(X, ldx, r, k, K, conj, mask) : make_double2(0.0, 0.0);
     const size_t o = (size_t)r * k_pad + k;
+    oz_digits(v.x, shift, S, planes + o, plane);
+    oz_digits(v.y, shift, S, planes + pstride + o, plane);
+    if (npl == 3) oz_digits(-v.y, shift, S, planes + 2 * pstride + o, plane);
+  }
+}
+
+// Columns of X (K rows x R columns, ld ldx) as operand rows. Pass 1: the exponent of each
+// column (threads across consecutive columns, coalesced). Pass 2: a 32 x 32 tile of X
+// staged in shared memory and written out transposed, so the digit stores run along k.
+constexpr int OZ_CT = 32;
+
+__global__ void __launch_bounds__(256) oz_cols_exp_kernel(int R, int K, const double2* X, int64_t ldx, int conj,
+                                                          int mask, int* ex, int* bad) {
+  __shared__ double red[8][OZ_CT];
+  const int j = blockIdx.x * OZ_CT + threadIdx.x;
+  double mx = 0.0;
+  bool nonfinite = false;
+  if (j < R)
+    for (int k = threadIdx.y; k < K; k += 8) {
+      const double2 v = oz_masked(X[(int64_t)k * ldx + j], j, k, conj, mask);
+      if (!oz_finite(v)) nonfinite = true;
+      else mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  if (nonfinite) atomicExch(bad, 1);
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < R) {
+    for (int t = 1; t < 8; ++t) mx = fmax(mx, red[t][threadIdx.x]);
+    ex[j] = mx > 0.0 ? ilogb(mx) + 2 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) oz_cols_digits_kernel(int R, int K, const double2* X, int64_t ldx, int conj,
+                                                             int mask, int S, int npl, int rows_pad, int k_pad,
+                                                             __nv_bfloat16* planes, const int* ex) {
+  __shared__ double2 tile[OZ_CT][OZ_CT + 1];   // [k][j]
+  const int k0 = blockIdx.x * OZ_CT, j0 = blockIdx.y * OZ_CT;
+  for (int i = threadIdx.y; i < OZ_CT; i += 8) {
+    const int k = k0 + i, j = j0 + threadIdx.x;
+    tile[i][threadIdx.x] = (k < K && j < R) ? oz_masked(X[(int64_t)k * ldx + j], j, k, conj, mask)
+                                            : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const size_t plane = (size_t)rows_pad * k_pad;
+  const size_t pstride = (size_t)S * plane;
+  const int k = k0 + threadIdx.x;
+  if (k >= k_pad) return;
+  for (int jj = threadIdx.y; jj < OZ_CT; jj += 8) {
+    const int j = j0 + jj;
+    if (j >= rows_pad) break;
+    const double2 v = tile[threadIdx.x][jj];
+    const int shift = 7 * S - (j < R ? ex[j] : 0);
+    const size_t o = (size_t)j * k_pad + k;
     oz_digits(v.x, shift, S, planes + o, plane);
     oz_digits(v.y, shift, S, planes + pstride + o, plane);
     if (npl == 3) oz_digits(-v.y, shift, S, planes + 2 * pstride + o, plane);
@@ -363,7 +424,7 @@ bool oz_supported() {
 }
 
 cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
-                     int S, int npl, int* bad, cudaStream_t s) {
+                     int S, int npl, int* bad, cudaStream_t s, bool cols) {
   if (S < 1 || S > kOzSlicesMax || (npl != 2 && npl != 3)) return cudaErrorInvalidValue;
   op.rows = rows;
   op.K = K;
@@ -374,9 +435,17 @@ cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X
   op.planes = (__nv_bfloat16*)mem;
   op.ex = (int*)((char*)mem + (size_t)npl * S * op.rows_pad * op.k_pad * 2);
   if (rows == 0) return cudaSuccess;
-  oz_split_rows_kernel<<<op.rows_pad, 256, 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
-                                                   op.planes, op.ex, bad);
-  LAUNCH_NOTE(1);
+  if (!cols) {
+    oz_split_rows_kernel<<<op.rows_pad, 256, 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
+                                                     op.planes, op.ex, bad);
+    LAUNCH_NOTE(1);
+  } else {
+    oz_cols_exp_kernel<<<(rows + OZ_CT - 1) / OZ_CT, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, op.ex, bad);
+    dim3 grid((op.k_pad + OZ_CT - 1) / OZ_CT, (op.rows_pad + OZ_CT - 1) / OZ_CT);
+    oz_cols_digits_kernel<<<grid, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
+                                                          op.planes, op.ex);
+    LAUNCH_NOTE(2);
+  }
   return cudaGetLastError();
 }
 

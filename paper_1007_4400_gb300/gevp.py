@@ -119,7 +119,7 @@ def load(build_if_missing: bool = True):
                                             C.POINTER(f64), f64, vp, i64, C.POINTER(i64), C.POINTER(f64),
                                             C.POINTER(f64), C.POINTER(i64)]
         L.gevp_assign_min_cost.argtypes = [i32, i32, C.POINTER(f64), C.POINTER(i64)]
-        L.gevp_zgemm_emulated.argtypes = [vp, i32, i32, i32, vp, i64, vp, i64, vp, i64, i32]
+        L.gevp_zgemm_emulated.argtypes = [vp, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp, i64, i32]
         L.gevp_reduce_emulated.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, C.POINTER(i64), i32]
         L.gevp_kernel_launches.argtypes = [vp]
         L.gevp_kernel_launches.restype = i64
@@ -200,17 +200,18 @@ def reduce(A: torch.Tensor, B: torch.Tensor, slices: int = 0):
     return L_, C_
 
 
-def zgemm_emulated(A: torch.Tensor, B: torch.Tensor, slices: int = 8) -> torch.Tensor:
-    """A B^H (A M x K, B N x K, complex128) emulated on the tensor cores with `slices`
-    7-bit digits per entry (gevp_zgemm_emulated)."""
+def zgemm_emulated(A: torch.Tensor, B: torch.Tensor, slices: int = 8, opA: str = "N", opB: str = "C") -> torch.Tensor:
+    """op(A) op(B) (complex128; op "N" = X, "C" = X^H) emulated on the tensor cores with
+    `slices` 7-bit digits per entry (gevp_zgemm_emulated). The default is A B^H."""
     _mat(A, "A"); _mat(B, "B")
-    M, K = A.shape
-    N = B.shape[0]
-    if B.shape[1] != K:
-        raise ValueError("A and B need the same number of columns")
+    oa, ob = {"N": 0, "C": 1}[opA], {"N": 0, "C": 1}[opB]
+    M, K = (A.shape[1], A.shape[0]) if oa else (A.shape[0], A.shape[1])
+    Kb, N = (B.shape[1], B.shape[0]) if ob else (B.shape[0], B.shape[1])
+    if Kb != K:
+        raise ValueError("op(A) and op(B) do not conform")
     h = _handle(A.device)
     D = torch.empty((M, N), dtype=torch.complex128, device=A.device)
-    st = load().gevp_zgemm_emulated(h, M, N, K, _ptr(A), A.stride(0) if K else 1, _ptr(B), B.stride(0) if K else 1,
+    st = load().gevp_zgemm_emulated(h, oa, ob, M, N, K, _ptr(A), max(A.stride(0), 1), _ptr(B), max(B.stride(0), 1),
                                     _ptr(D), max(N, 1), int(slices))
     _check(st, h)
     return D

@@ -63,6 +63,23 @@ def test_random_within_bound(cuda, M, N, K):
             assert err.max() <= 64 * math.sqrt(2 * K) * 2.0 ** (-7 * S)
 
 
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("C", "C"), ("C", "N"), ("N", "C")])
+def test_op_variants(cuda, opA, opB):
+    # rows of op(A) and columns of op(B) come from rows or (transposed) columns of the
+    # stored matrices; every combination against the plain product
+    from paper_1007_4400_gb300 import gevp
+    M, N, K = 150, 97, 777
+    rng = np.random.default_rng(2500 + len(opA + opB) + (opA == "C") * 7 + (opB == "C") * 13)
+    opa = crandn(rng, M, K) * np.exp(rng.uniform(-3, 3, (M, 1)))
+    opb = crandn(rng, K, N) * np.exp(rng.uniform(-3, 3, (1, N)))
+    A = opa if opA == "N" else opa.conj().T
+    B = opb if opB == "N" else opb.conj().T
+    D = gevp.zgemm_emulated(T(A, cuda), T(B, cuda), slices=8, opA=opA, opB=opB).cpu().numpy()
+    ref = opa @ opb
+    err = np.abs(D - ref) / scale(opa, opb.T)
+    assert err.max() <= 64 * math.sqrt(2 * K) * 2.0 ** -56
+
+
 def test_zero_rows_and_empty_k(cuda):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(3000)
