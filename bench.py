@@ -200,6 +200,14 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+def measured_peaks() -> dict:
+    """The measured peaks of this machine's GPUs (MEASURED_PEAKS.json), or {}."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,6 +438,9 @@ def main():
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
+    # live timing of the GEMM kernels over the timed region (an event pair per launch on
+    # its own stream: about 0.2 % of the step)
+    gevp.kernel_timing(True)
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -441,6 +452,8 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
+    gevp.kernel_timing(False)
+    live = gevp.kernel_timing_read()
     launches = (gevp.kernel_launches(local) - launches0) // max(1, args.steps)
     ms_total = e0.elapsed_time(e1)
     ms_step = max_over_ranks(ms_total / args.steps, world, dev)
@@ -451,43 +464,63 @@ def main():
     value = world * nominal / (ms_step * 1e-3) / 1e12
     executed_tflops = world * flops / (ms_step * 1e-3) / 1e12
 
-    # ---- roofline of the dominant kernel: the FP64 complex GEMM of the Chebyshev filter
-    # step (C . Y, n x n times n x m), timed with CUDA events on the launching stream.
-    C = torch.empty((n, n), dtype=torch.complex128, device=dev)
-    Lf, C = gevp.reduce(seq.A[-1], seq.B)
-    Y = torch.randn((n, m), dtype=torch.complex128, device=dev)
-    deg = 16
-    gevp.chebyshev_filter(C, Y, 2, 5.0, 60.0, -3.0)
-    torch.cuda.synchronize()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    reps = 3
-    for _ in range(reps):
-        gevp.chebyshev_filter(C, Y, deg, 5.0, 60.0, -3.0)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ms_launch = f0.elapsed_time(f1) / (reps * deg)
-    alg_flops = 8.0 * n * n * m
-    achieved = alg_flops / (ms_launch * 1e-3) / 1e12
-    # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock x 2 flop x SM clock
-    # (2070 MHz max); ncu measures the FP64 pipe at 98.8 % busy in this kernel, consistent
-    # with this peak. The simple FMA/DMMA probes (reported below) reach 85-90 % of it.
+    # ---- roofline of the dominant kernel, from the live timing of the timed region: the
+    # GEMM class with the larger device time (the emulated product when the reduction and
+    # the n^2 m products are emulated, else the FP64 complex GEMM)
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
+    # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock x 2 flop
     fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "zgemm_filter_n2048_m140.json")
-    if os.path.exists(prof) and n == 2048 and m == 140:
-        try:
-            traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
-    roofline = {"bound": "alu", "kernel": "zgemm_kernel (FP64 complex, filter step C.Y)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": traffic,
-                "peak_source": "FP64 unit count x measured max SM clock (152 SM x 2 FMA/clk x 2 flop)",
-                "alg_flops_per_launch": alg_flops, "alg_bytes_per_launch": 16.0 * n * n + 48.0 * n * m,
-                "ms_per_launch": ms_launch}
+    mp = measured_peaks()
+    oz, zg = live["oz_gemm_kernel"], live["zgemm_kernel"]
+    if oz["ms"] >= zg["ms"] and oz["launches"] > 0:
+        ms_launch = oz["ms"] / oz["launches"]
+        achieved = oz["exec_flop"] / (oz["ms"] * 1e-3) / 1e12
+        peak = mp.get("bf16_tflops_sustained") or 1700.0
+        roofline = {"bound": "tensor", "kernel": "oz_gemm_kernel (emulated FP64 complex product, 8 digits)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": "BF16 sustained, of measured (MEASURED_PEAKS.json)",
+                    "work": "executed BF16 flop of the digit-pair products (36 x the FP64-equivalent 8 flop per "
+                            "complex multiply-add over the K ranges processed)",
+                    "launches_per_step": oz["launches"] / max(1, args.steps), "ms_per_launch": ms_launch,
+                    "fp64_equiv_tflops": oz["alg_flop"] / (oz["ms"] * 1e-3) / 1e12,
+                    "share_of_step": oz["ms"] / max(1e-9, ms_total), "zgemm_share_of_step": zg["ms"] / max(1e-9, ms_total),
+                    "traffic_note": "launch shapes vary within the step: traffic is given for the isolated launch"}
+        # isolated reference launch with the shape of the committed ncu capture (A B^H, n 2048)
+        g = torch.Generator(device=dev).manual_seed(13)
+        Ai = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
+        Bi = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
+        for _ in range(2):
+            gevp.zgemm_emulated(Ai, Bi, 8)
+        torch.cuda.synchronize()
+        gevp.kernel_timing(True)
+        for _ in range(5):
+            gevp.zgemm_emulated(Ai, Bi, 8)
+        torch.cuda.synchronize()
+        gevp.kernel_timing(False)
+        iso = gevp.kernel_timing_read()["oz_gemm_kernel"]
+        iso_ms = iso["ms"] / max(1, iso["launches"])
+        iso_ach = iso["exec_flop"] / (iso["ms"] * 1e-3) / 1e12
+        traffic = None
+        prof = os.path.join(ROOT, "profiles", "oz_gemm_n2048.json")
+        if os.path.exists(prof):
+            try:
+                traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
+            except (OSError, ValueError):
+                traffic = None
+        burst = mp.get("bf16_tflops") or 1900.0
+        roofline["isolated"] = {"shape": "A B^H, 2048 x 2048 x 2048 complex", "ms_per_launch": iso_ms,
+                                "achieved": iso_ach, "peak": burst, "frac": iso_ach / burst, "traffic": traffic,
+                                "fp64_equiv_tflops": iso["alg_flop"] / (iso["ms"] * 1e-3) / 1e12}
+        del Ai, Bi
+    else:
+        ms_launch = zg["ms"] / max(1, zg["launches"])
+        achieved = zg["alg_flop"] / (max(zg["ms"], 1e-9) * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "zgemm_kernel (FP64 complex GEMM, all launches of the step)",
+                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "traffic": None,
+                    "peak_source": "FP64 unit count x measured max SM clock (152 SM x 2 FMA/clk x 2 flop)",
+                    "launches_per_step": zg["launches"] / max(1, args.steps), "ms_per_launch": ms_launch,
+                    "share_of_step": zg["ms"] / max(1e-9, ms_total)}
 
     # ---- plain FP64 cold-start GPU solver on the same sequence (the comparison form)
     compare = None

@@ -122,11 +122,19 @@ struct BatchPlan {
   // emulated reduction: digit forms of every k-point's L^-1 (left operand) and L^-H (right
   // operand), made once per call, plus one k-point's worth of scratch for tril(A) and T
   int oz_S = 0;
+  int oz_key = 0;   // reduce_slices the plan (and its captured round) was built for
   char* oz_mem = nullptr;
   size_t oz_bytes = 0;
   std::vector<OzOperand> ozLA, ozLB;
   OzOperand ozAB, ozTA;
   char* oz_scratch = nullptr;
+  // W = C Q of every round: the digits of each k-point's C (made once per step) and one
+  // k-point's block (made per round, inside the captured round)
+  std::vector<OzOperand> ozC;
+  OzOperand ozQ;
+  char* oz_cq = nullptr;
+  size_t oz_cq_bytes = 0;
+  char* oz_qs = nullptr;   // the block's digits (inside oz_cq)
   int* oz_flags = nullptr;   // device: [0] kernel error code, [1] non-finite entry
   std::vector<cudaEvent_t> ev;
 };
@@ -137,6 +145,7 @@ void batch_release(BatchPlan* P) {
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->arena) cudaFree(P->arena);
   if (P->oz_mem) cudaFree(P->oz_mem);
+  if (P->oz_cq) cudaFree(P->oz_cq);
   if (P->hD) cudaFreeHost(P->hD);
   for (auto e : P->ev) cudaEventDestroy(e);
   delete P;
@@ -497,7 +506,16 @@ void enqueue_orth(BatchPlan* P, cudaStream_t s, bool tune) {
 
 void enqueue_rr(BatchPlan* P, cudaStream_t s, bool tune) {
   const int np = P->np, mmax = P->mmax;
-  launch(P, P->c_wt, s, tune);
+  if (P->oz_S > 0 && (int)P->ozC.size() == np) {
+    // W = C Q emulated per k-point; a converged k-point's launches do nothing
+    for (int k = 0; k < np; ++k) {
+      const BDesc& d = P->hD[k];
+      oz_split(P->ozQ, P->oz_qs, d.m, d.n, d.Q, d.m, 0, 0, P->oz_S, 3, P->oz_flags + 1, s, true, d.flags);
+      oz_gemm(P->ozC[k], P->ozQ, 0, 0, d.Wt, d.m, P->oz_flags, s, d.flags);
+    }
+  } else {
+    launch(P, P->c_wt, s, tune);
+  }
   launch(P, P->c_g, s, tune);
   bk_heev_prep(P->dD, np, mmax, s);
   for (int it = 0; it <= P->refine; ++it) {
@@ -640,8 +658,10 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
 
   // ---- plan (reused while the shapes and modes are unchanged)
   BatchPlan*& P = ctx_batch(h);
+  // the captured round graph embeds the emulated products or the grouped FP64 one
+  const int oz_want = (o.reduce_slices > 0 && oz_supported()) ? o.reduce_slices : 0;
   bool same = P && P->np == nk && P->prec == o.filter_prec && P->deg_steps == o.deg_max &&
-              P->refine == o.refine_iters && P->kl == kl;
+              P->refine == o.refine_iters && P->kl == kl && P->oz_key == oz_want;
   if (same)
     for (int k = 0; k < nk && same; ++k) same = P->n[k] == n[k] && P->m[k] == m[k] && P->nev[k] == nev[k];
   if (!same) {
@@ -652,6 +672,7 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
     }
     P = new BatchPlan();
     P->np = nk;
+    P->oz_key = oz_want;
     P->prec = o.filter_prec;
     P->nsplit = nsplit;
     P->tc = tc;
@@ -730,7 +751,7 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
       return GEVP_ERR_NOT_HPD;
     }
   // digit forms of L^-1 for the emulated reduction (o.reduce_slices digits per entry)
-  P->oz_S = (o.reduce_slices > 0 && oz_supported() && P->nmax <= 30720) ? o.reduce_slices : 0;
+  P->oz_S = P->nmax <= 30720 ? P->oz_key : 0;
   if (P->oz_S > 0) {
     const int S = P->oz_S;
     size_t need = 256, scratch = 0;
@@ -761,6 +782,22 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
       q += oz_operand_bytes(nk_, nk_, S, 3);
     }
     P->oz_scratch = q;
+    // digits of C (one per k-point) and of one block (the largest)
+    size_t cq = 256, qs = 0;
+    for (int k = 0; k < np; ++k) {
+      cq += oz_operand_bytes((int)n[k], (int)n[k], S, 2);
+      qs = std::max(qs, oz_operand_bytes(P->hD[k].m, (int)n[k], S, 3));
+    }
+    cq += qs;
+    if (cq > P->oz_cq_bytes) {
+      if (P->oz_cq) cudaFree(P->oz_cq);
+      P->oz_cq = nullptr;
+      P->oz_cq_bytes = 0;
+      BCK(cudaMalloc(&P->oz_cq, cq));
+      P->oz_cq_bytes = cq;
+    }
+    P->oz_qs = P->oz_cq + (cq - qs);
+    P->ozC.assign(np, OzOperand{});
   }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, evt(P, EV_T0), evt(P, EV_CHOL));
@@ -836,6 +873,15 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
       launch(P, P->c_red2, s, tune);
     }
     bk_herm_sum(P->dD, np, P->nmax, s);
+    if (P->oz_S > 0) {
+      // the digits of every C for the rounds' W = C Q
+      char* q = P->oz_cq;
+      for (int k = 0; k < np; ++k) {
+        const BDesc& d = P->hD[k];
+        BCK(oz_split(P->ozC[k], q, (int)n[k], (int)n[k], d.C, n[k], 0, 0, P->oz_S, 2, P->oz_flags + 1, s));
+        q += oz_operand_bytes((int)n[k], (int)n[k], P->oz_S, 2);
+      }
+    }
     BCK(cudaEventRecord(evt(P, EV_RED), s));
     // ---- bounds of C (and ||A||_2)
     bk_to_c32(P->dD, np, P->nmax, 0, s);

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(1024) b_potrf_small(const BDesc* D) {
   const BDesc& d = D[blockIdx.x];
   if (!live(d)) return;
   __shared__ int fail;
+  __shared__ double pinv;   // 1 / pivot: one FP64 division per column, not one per thread
   const int m = d.m;
   double2* A = d.Gw;
   if (threadIdx.x == 0) fail = 0;
@@ -171,11 +172,15 @@ __global__ void __launch_bounds__(1024) b_potrf_small(const BDesc* D) {
     if (threadIdx.x == 0) {
       double v = A[j * m + j].x;
       if (!(v > 0.0)) fail = j + 1;
-      else A[j * m + j] = make_double2(sqrt(v), 0.0);
+      else {
+        const double r = sqrt(v);
+        A[j * m + j] = make_double2(r, 0.0);
+        pinv = 1.0 / r;
+      }
     }
     __syncthreads();
     if (fail) break;
-    const double inv = 1.0 / A[j * m + j].x;
+    const double inv = pinv;
     for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * m + j] = zscale(A[i * m + j], inv);
     __syncthreads();
     const int rem = m - j - 1;
@@ -203,10 +208,13 @@ __global__ void __launch_bounds__(1024) b_trtri_small(const BDesc* D) {
   const int m = d.m;
   const double2* L = d.Gw;
   double2* X = d.Gwi;
+  // reciprocals of the diagonal, one division per row (m <= 1024)
+  __shared__ double rdiag[1024];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) rdiag[i] = 1.0 / L[i * m + i].x;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) X[e] = make_double2(0.0, 0.0);
   __syncthreads();
   for (int i = 0; i < m; ++i) {
-    const double inv = 1.0 / L[i * m + i].x;
+    const double inv = rdiag[i];
     for (int c = threadIdx.x; c <= i; c += blockDim.x) {
       double2 s = make_double2(c == i ? 1.0 : 0.0, 0.0);
       for (int k = c; k < i; ++k) {

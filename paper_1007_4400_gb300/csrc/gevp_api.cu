@@ -333,14 +333,19 @@ void reduce_into_ws(int64_t n, const double2* Linv, const double2* A, int64_t ld
 // per entry): T = L^-1 tril_half(A) and M = T L^-H as digit-form products, then C = M + M^H.
 // side 0 runs on the main stream, side 1 on the pipeline's side stream (own scratch). The
 // digit forms of L^-1 are made once per factorisation of B, on the main stream.
+// the device status words of the emulated products ([0] error code, [1] non-finite entry)
+gevp_status oz_flags_ready(gevp_ctx* h) {
+  if (h->ozflags) return GEVP_OK;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, 2 * sizeof(int)));
+  CK(cudaMemsetAsync(p, 0, 2 * sizeof(int), h->stream));
+  h->ozflags = (int*)p;
+  return GEVP_OK;
+}
+
 // device scratch of the emulated products: ozmem[side] of at least `need` bytes
 gevp_status oz_reserve(gevp_ctx* h, int side, size_t need) {
-  if (!h->ozflags) {
-    void* p = nullptr;
-    CK(cudaMalloc(&p, 2 * sizeof(int)));
-    CK(cudaMemsetAsync(p, 0, 2 * sizeof(int), h->stream));
-    h->ozflags = (int*)p;
-  }
+  TRY(oz_flags_ready(h));
   if (need <= h->ozmem_bytes[side]) return GEVP_OK;
   // the other stream may still read this side's (or, for side 0, the shared) operands
   cudaDeviceSynchronize();
@@ -1072,6 +1077,11 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
   for (int l = 0; l < nprob; ++l)
     if (!A[l] || !B[l]) return GEVP_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
+  // the emulated products serve this solve only (the per-step entry points stay FP64)
+  struct OzScope {
+    gevp_ctx* h;
+    ~OzScope() { h->oz_slices = 0; }
+  } oz_scope{h};
   h->oz_slices = o.reduce_slices;
   TRY(ensure(h, n, m));
   TRY(ensure_pipeline(h));

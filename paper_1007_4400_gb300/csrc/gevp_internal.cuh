@@ -275,11 +275,12 @@ bool oz_supported();
 // rows of X (cols = false; X is rows x K) or its columns (cols = true; X is K x rows) as
 // operand rows, conjugated if conj, mask 1: k >= r with the diagonal halved, 2: k <= r,
 // 3: k >= r; into digit form in `mem` (oz_operand_bytes); *bad = 1 on a non-finite entry
+// active: nullable device flag, 0 = the launch does nothing (a converged batch problem)
 cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
-                     int S, int npl, int* bad, cudaStream_t s, bool cols = false);
+                     int S, int npl, int* bad, cudaStream_t s, bool cols = false, const int* active = nullptr);
 // D (A.rows x B.rows) = op(A) op(B); triA 1: op(A) lower; triB 1: op(B) lower, 2: upper
 cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
-                    cudaStream_t s);
+                    cudaStream_t s, const int* active = nullptr);
 
 // ---------------------------------------------------------------- deviation angles
 // slices of the column-norm reduction (part needs slices * k doubles)
@@ -310,6 +311,15 @@ void probe_peaks(double* fp64_fma_tflops, double* fp64_dmma_tflops, double* fp32
 // ---------------------------------------------------------------- launch accounting
 extern int64_t g_launches;
 #define LAUNCH_NOTE(k) (::gevp::g_launches += (k))
+
+// ---------------------------------------------------------------- live kernel timing
+// Classes: 0 the FP64 complex GEMM (zgemm_kernel), 1 the emulated product (oz_gemm_kernel).
+// kt_begin records an event on s and returns it (only call when kt_enabled()); kt_end
+// records the closing event with the launch's algorithmic and executed flop.
+bool kt_enabled();
+void* kt_begin(cudaStream_t s);
+void kt_end(void* begin, int cls, double alg, double exec, cudaStream_t s);
+double tiled_product_flops(int M, int N, int K, int triA, int triB, int triD);
 
 // ---------------------------------------------------------------- error handling
 #define GEVP_CUDA_TRY(x)                                   \

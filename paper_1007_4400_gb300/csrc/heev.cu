@@ -2,8 +2,10 @@
 //
 // One SM executes FP64 at about 1.7 FMA per clock on this part, so an FP64 Jacobi in one
 // CTA would take milliseconds. Instead:
-//   1. parallel-ordered two-sided Jacobi in FP32 in one CTA (FP32 runs at 128 FMA per
-//      clock per SM), giving eigenvectors accurate to about 1e-6;
+//   1. parallel-ordered two-sided Jacobi in FP32 (FP32 runs at 128 FMA per clock per SM),
+//      giving eigenvectors accurate to about 1e-6: one CTA below m = 32, the eight CTAs
+//      of a thread-block cluster sharing G through distributed shared memory up to
+//      m = 256, all SMs (cooperative launch) above;
 //   2. Ogita & Aishima's iterative refinement for symmetric/Hermitian eigenvector
 //      matrices (Japan J. Ind. Appl. Math. 35, 2018), which converges quadratically and
 //      consists of four FP64 GEMMs per step spread over all SMs. Pairs closer than the
@@ -60,11 +62,35 @@ __device__ __forceinline__ float2 ld2(const float2* p) {
   else return *p;
 }
 
+// Element access to G for the Jacobi rounds: a plain matrix (shared or global memory, the
+// one-CTA forms), a global matrix read through L2 (the cooperative form: other CTAs wrote
+// it and L1 is not coherent across SMs), or row bands held in the shared memory of the CTAs
+// of a thread-block cluster (the cluster form; rows [c mb, (c + 1) mb) in CTA c).
+struct GPlain {
+  float2* g;
+  int m;
+  __device__ __forceinline__ float2 ld(int i, int j) const { return g[i * m + j]; }
+  __device__ __forceinline__ void st(int i, int j, float2 v) const { g[i * m + j] = v; }
+};
+struct GL2 {
+  float2* g;
+  int m;
+  __device__ __forceinline__ float2 ld(int i, int j) const { return __ldcg(g + i * m + j); }
+  __device__ __forceinline__ void st(int i, int j, float2 v) const { g[i * m + j] = v; }
+};
+struct GBand {
+  float2* const* band;   // per cluster rank: the generic address of that CTA's band
+  int m, mb;
+  __device__ __forceinline__ float2* at(int i, int j) const { return band[i / mb] + (i % mb) * m + j; }
+  __device__ __forceinline__ float2 ld(int i, int j) const { return *at(i, j); }
+  __device__ __forceinline__ void st(int i, int j, float2 v) const { *at(i, j) = v; }
+};
+
 // Rotation of pair k of round `step`: U = [[c, s], [-s conj(ph), c conj(ph)]] acting on
 // columns (p, q), stored as (c, s, Re ph, Im ph); identity for the dummy index q = m of
 // odd orders and for couplings below FP32 significance relative to the diagonal.
-template <bool L2 = false>
-__device__ __forceinline__ void jacobi_pair_params(const float2* G, int m, int np, int step, int k, float4* U,
+template <class Acc>
+__device__ __forceinline__ void jacobi_pair_params(const Acc& G, int m, int np, int step, int k, float4* U,
                                                    int (*PQ)[2]) {
   int p, q;
   block_pair(step, k, np, &p, &q);
@@ -72,11 +98,11 @@ __device__ __forceinline__ void jacobi_pair_params(const float2* G, int m, int n
   PQ[k][1] = q;
   float4 u = make_float4(1.f, 0.f, 1.f, 0.f);
   if (q < m) {
-    float2 apq = ld2<L2>(G + p * m + q);
+    float2 apq = G.ld(p, q);
     // |g_pq| without under/overflow: the phase g_pq / |g_pq| must stay unit-modulus
     // or the rotation stops being unitary (squares of tiny off-diagonals are denormal)
     float r = hypotf(apq.x, apq.y);
-    float app = ld2<L2>(G + p * m + p).x, aqq = ld2<L2>(G + q * m + q).x;
+    float app = G.ld(p, p).x, aqq = G.ld(q, q).x;
     if (r > 1e-30f && r > 1e-10f * (fabsf(app) + fabsf(aqq))) {
       float tau = (aqq - app) / (2.f * r);
       float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
@@ -96,8 +122,8 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // e < npairs^2, a = row pair, b = column pair), and Z <- Z U into independent row pieces
 // (tasks after those). Every element of G is read from G and written to Gout once per
 // step (Gout = G in place, or the other buffer of a ping-pong pair).
-template <bool L2 = false>
-__device__ __forceinline__ void jacobi_apply(const float2* G, float2* Gout, float2* Z, int m, int npairs, int e,
+template <class Acc, bool ZL2>
+__device__ __forceinline__ void jacobi_apply(const Acc& G, const Acc& Gout, float2* Z, int m, int npairs, int e,
                                              const float4* U, const int (*PQ)[2]) {
   if (e < npairs * npairs) {
     const int a = e / npairs, b = e % npairs;
@@ -105,10 +131,10 @@ __device__ __forceinline__ void jacobi_apply(const float2* G, float2* Gout, floa
     const bool qv = q < m, sv = s < m;
     const float4 ua = U[a], ub = U[b];
     const float2 z0 = make_float2(0.f, 0.f);
-    float2 gpr = ld2<L2>(G + p * m + r);
-    float2 gps = sv ? ld2<L2>(G + p * m + s) : z0;
-    float2 gqr = qv ? ld2<L2>(G + q * m + r) : z0;
-    float2 gqs = (qv && sv) ? ld2<L2>(G + q * m + s) : z0;
+    float2 gpr = G.ld(p, r);
+    float2 gps = sv ? G.ld(p, s) : z0;
+    float2 gqr = qv ? G.ld(q, r) : z0;
+    float2 gqs = (qv && sv) ? G.ld(q, s) : z0;
     // columns (r, s) with U_b: x_r' = c x_r - s conj(ph) x_s, x_s' = s x_r + c conj(ph) x_s
     {
       const float c = ub.x, sn = ub.y;
@@ -145,10 +171,10 @@ __device__ __forceinline__ void jacobi_apply(const float2* G, float2* Gout, floa
       gpr.y = 0.f;
       gqs.y = 0.f;
     }
-    Gout[p * m + r] = gpr;
-    if (sv) Gout[p * m + s] = gps;
-    if (qv) Gout[q * m + r] = gqr;
-    if (qv && sv) Gout[q * m + s] = gqs;
+    Gout.st(p, r, gpr);
+    if (sv) Gout.st(p, s, gps);
+    if (qv) Gout.st(q, r, gqr);
+    if (qv && sv) Gout.st(q, s, gqs);
   } else {
     const int t = e - npairs * npairs;
     const int i = t / npairs, b = t % npairs;
@@ -157,7 +183,7 @@ __device__ __forceinline__ void jacobi_apply(const float2* G, float2* Gout, floa
     const float4 u = U[b];
     const float c = u.x, sn = u.y;
     const float2 phc = make_float2(u.z, -u.w);
-    const float2 zr = ld2<L2>(Z + i * m + r), zs = cmulf(ld2<L2>(Z + i * m + s), phc);
+    const float2 zr = ld2<ZL2>(Z + i * m + r), zs = cmulf(ld2<ZL2>(Z + i * m + s), phc);
     Z[i * m + r] = make_float2(c * zr.x - sn * zs.x, c * zr.y - sn * zs.y);
     Z[i * m + s] = make_float2(sn * zr.x + c * zs.x, sn * zr.y + c * zs.y);
   }
@@ -201,9 +227,11 @@ __device__ void jacobi32_body(int m, float2* Gg, float2* Z, float* w, int* perm,
     if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
     off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
-      for (int k = tid; k < npairs; k += JT) jacobi_pair_params(G, m, np, step, k, U, PQ);
+      const GPlain Ga{G, m};
+      for (int k = tid; k < npairs; k += JT) jacobi_pair_params(Ga, m, np, step, k, U, PQ);
       __syncthreads();
-      for (int e = tid; e < npairs * npairs + m * npairs; e += JT) jacobi_apply(G, G, Z, m, npairs, e, U, PQ);
+      for (int e = tid; e < npairs * npairs + m * npairs; e += JT)
+        jacobi_apply<GPlain, false>(Ga, Ga, Z, m, npairs, e, U, PQ);
       __syncthreads();
     }
   }
@@ -264,10 +292,11 @@ __global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, flo
     if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
     off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
-      for (int k = tid; k < npairs; k += JT) jacobi_pair_params<true>(Gc, m, np, step, k, U, PQ);
+      const GL2 Ac{Gc, m}, An{Gn, m};
+      for (int k = tid; k < npairs; k += JT) jacobi_pair_params(Ac, m, np, step, k, U, PQ);
       __syncthreads();
       for (int e = gtid; e < npairs * npairs + m * npairs; e += gsz)
-        jacobi_apply<true>(Gc, Gn, Z, m, npairs, e, U, PQ);
+        jacobi_apply<GL2, true>(Ac, An, Z, m, npairs, e, U, PQ);
       grid.sync();
       float2* t = Gc;
       Gc = Gn;
@@ -285,6 +314,100 @@ __global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, flo
     perm[r] = i;
     w[r] = wi;
   }
+}
+
+// Cluster form for mid-size orders: the rounds of jacobi32_body spread over the kJC CTAs
+// of one thread-block cluster. G lives in the CTAs' shared memory as row bands (two
+// buffers: a round reads one and writes the other, so CTAs still computing the round's
+// rotations never see rotated entries), read and written through distributed shared
+// memory; one cluster barrier per round instead of one CTA doing every 2 x 2 block. The
+// arithmetic of every element is that of jacobi32_body, so the results are identical. Z
+// stays in global memory (read through L2). Gin (m x m) is read, not modified.
+constexpr int kJC = 8;
+constexpr int kJClusterMax = 256;
+
+__global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const float2* Gin, float2* Z, float* w,
+                                                                 int* perm, int max_sweeps) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ float2 jband[];   // [2][mb][m]
+  __shared__ float4 U[512];
+  __shared__ int PQ[512][2];
+  __shared__ float red[32];
+  __shared__ float part[64];          // this CTA's partial sums: [0] ||G||_F^2, [1 + sweep] off-norm
+  __shared__ float2* bandp[2][kJC];   // generic addresses of every CTA's two bands
+  const int tid = threadIdx.x;
+  const int rank = (int)cl.block_rank();
+  const int mb = (m + kJC - 1) / kJC;
+  if (tid < kJC) {
+    bandp[0][tid] = cl.map_shared_rank(jband, tid);
+    bandp[1][tid] = cl.map_shared_rank(jband + mb * m, tid);
+  }
+  // own band of G into buffer 0 (rows past m are never addressed)
+  const int r0 = rank * mb;
+  for (int e = tid; e < mb * m; e += JT) {
+    const int r = r0 + e / m;
+    jband[e] = r < m ? Gin[r * m + (e % m)] : make_float2(0.f, 0.f);
+  }
+  const int gtid = rank * JT + tid, gsz = kJC * JT;
+  for (int e = gtid; e < m * m; e += gsz) Z[e] = make_float2((e / m) == (e % m) ? 1.f : 0.f, 0.f);
+  const int np = (m % 2) ? m + 1 : m;
+  const int npairs = np / 2;
+  const int rows = max(0, min(mb, m - r0));
+  float f = 0.f;
+  for (int e = tid; e < rows * m; e += JT) { float2 g = jband[e]; f += g.x * g.x + g.y * g.y; }
+  f = block_sum(f, red);
+  if (tid == 0) part[0] = f;
+  cl.sync();
+  // every CTA sums the partials in the same order: the same decisions everywhere
+  auto cluster_sum = [&](int slot) {
+    float t = 0.f;
+    for (int c = 0; c < kJC; ++c) t += *cl.map_shared_rank(&part[slot], c);
+    return t;
+  };
+  const float fro2 = cluster_sum(0);
+  const float tol2 = 1e-16f * fro2;
+  float off_prev = 3.0e38f;
+  int cur = 0;
+  if (max_sweeps > 62) max_sweeps = 62;
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
+    float off = 0.f;
+    const float2* Gc = jband + cur * mb * m;
+    for (int e = tid; e < rows * m; e += JT) {
+      const int i = r0 + e / m, j = e % m;
+      if (i != j) { float2 g = Gc[e]; off += g.x * g.x + g.y * g.y; }
+    }
+    off = block_sum(off, red);
+    if (tid == 0) part[1 + sweep] = off;
+    cl.sync();
+    off = cluster_sum(1 + sweep);
+    if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
+    off_prev = off;
+    for (int step = 0; step < np - 1; ++step) {
+      const GBand Ac{bandp[cur], m, mb}, An{bandp[cur ^ 1], m, mb};
+      for (int k = tid; k < npairs; k += JT) jacobi_pair_params(Ac, m, np, step, k, U, PQ);
+      __syncthreads();
+      for (int e = gtid; e < npairs * npairs + m * npairs; e += gsz)
+        jacobi_apply<GBand, true>(Ac, An, Z, m, npairs, e, U, PQ);
+      cl.sync();
+      cur ^= 1;
+    }
+  }
+  if (rank == 0) {
+    const GBand Ac{bandp[cur], m, mb};
+    for (int i = tid; i < m; i += JT) {
+      const float wi = Ac.ld(i, i).x;
+      int r = 0;
+      for (int j = 0; j < m; ++j) {
+        const float wj = Ac.ld(j, j).x;
+        r += (wj < wi) || (wj == wi && j < i);
+      }
+      perm[r] = i;
+      w[r] = wi;
+    }
+  }
+  // no CTA leaves while rank 0 may still read its shared memory
+  cl.sync();
 }
 
 __global__ void __launch_bounds__(JT) jacobi32_kernel(int m, float2* G, float2* Z, float* w, int* perm,
@@ -549,6 +672,42 @@ bool jacobi32_coop(int m, float2* G, float2* Gb, float2* Z, float* w, int* perm,
   return true;
 }
 
+// Cluster Jacobi for 32 <= m <= kJClusterMax; false if it cannot be launched (then the
+// caller runs the one-CTA kernel).
+bool jacobi32_cluster(int m, const float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
+  if (m < 32 || m > kJClusterMax) return false;
+  const int mb = (m + kJC - 1) / kJC;
+  const size_t smem = (size_t)2 * mb * m * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(jacobi32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * ((kJClusterMax + kJC - 1) / kJC) * kJClusterMax * sizeof(float2))) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kJC, 1, 1);
+  cfg.blockDim = dim3(JT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kJC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, jacobi32_cluster_kernel, m, G, Z, w, perm, max_sweeps) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  LAUNCH_NOTE(1);
+  return true;
+}
+
 void jacobi32(int m, float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
   jacobi32_kernel<<<1, JT, jacobi_smem(m), s>>>(m, G, Z, w, perm, max_sweeps);
   LAUNCH_NOTE(1);
@@ -577,10 +736,13 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   LAUNCH_NOTE(1);
   // large orders on all SMs (cooperative launch); otherwise, or if that launch is not
   // possible, one CTA
-  // (the FP64 scratch E, unused until the refinement, holds the second FP32 buffer)
-  const bool coop = m > kJacobiSmemMax && jacobi32_coop(m, w.G32, (float2*)w.E, w.Z32, w.w32, w.perm, 40,
-                                                        (float*)(w.scal + 16), s);
-  if (!coop) {
+  // 32 <= m <= 256 on the eight CTAs of a cluster; larger orders on all SMs (cooperative
+  // launch; the FP64 scratch E, unused until the refinement, holds its second FP32 buffer);
+  // small ones, or when neither launch is possible, in one CTA
+  bool done = jacobi32_cluster(m, w.G32, w.Z32, w.w32, w.perm, 40, s);
+  if (!done && m > kJacobiSmemMax)
+    done = jacobi32_coop(m, w.G32, (float2*)w.E, w.Z32, w.w32, w.perm, 40, (float*)(w.scal + 16), s);
+  if (!done) {
     jacobi32_kernel<<<1, JT, jacobi_smem(m), s>>>(m, w.G32, w.Z32, w.w32, w.perm, 40);
     LAUNCH_NOTE(1);
   }

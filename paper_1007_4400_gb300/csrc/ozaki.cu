@@ -23,7 +23,7 @@
 // K u sum_k |a_ik||b_kj| being of the same order for S = 8.
 //
 // GEMM kernel: one CTA per 128 x 128 tile of the real or the imaginary part of D. Warp 8
-// issues TMA loads (3D maps: k, row, digit; 128-byte swizzle; four stages), warp 9 issues
+// issues TMA loads (3D maps: k, row, digit; 128-byte swizzle; six stages), warp 9 issues
 // the MMAs of one unit (digit pair, K chunk) into one of two TMEM accumulators (128
 // columns each) while warps 0-7 drain the other: each thread owns one row and 64 columns,
 // converts the exact FP32 sums to integers and adds them up per level; at the end of a
@@ -43,7 +43,7 @@ namespace {
 constexpr int OZ_TM = 128;
 constexpr int OZ_TN = 128;
 constexpr int OZ_TK = 64;
-constexpr int OZ_ST = 4;
+constexpr int OZ_ST = 6;
 constexpr int OZ_KCHUNK = 2048;
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = (OZ_EPI_WARPS + 2) * 32;
@@ -68,17 +68,21 @@ struct OzParams {
   double2* D;
   int64_t ldd;
   int* err;
+  const int* active;   // nullable device flag: 0 = skip the whole launch (a converged problem)
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
+  if (p.active && *p.active == 0) return;   // uniform: before any barrier or TMEM allocation
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[OZ_ST], empty[OZ_ST], tfull[2], tempty[2];
   __shared__ uint32_t tmem_sh;
   __shared__ uint8_t pair_s[OZ_MAXPAIRS], pair_t[OZ_MAXPAIRS], pair_last[OZ_MAXPAIRS];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int part = blockIdx.y / p.mt;   // 0: real part of D, 1: imaginary part
-  const int m0 = (blockIdx.y % p.mt) * OZ_TM;
+  // the real- and imaginary-part tiles of the same rows are launched next to each other:
+  // they read the same B tiles (first half of the embedding's K) while both are in L2
+  const int part = blockIdx.y & 1;   // 0: real part of D, 1: imaginary part
+  const int m0 = (blockIdx.y >> 1) * OZ_TM;
   const int n0 = blockIdx.x * OZ_TN;
   // K range of the tile from the triangular structure, in whole 64-blocks
   int klo = 0, khi = p.k_pad;
@@ -292,7 +296,9 @@ __device__ __forceinline__ void oz_digits(double x, int shift, int S, __nv_bfloa
 
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, const double2* X, int64_t ldx, int conj,
                                                             int mask, int S, int npl, int rows_pad, int k_pad,
-                                                            __nv_bfloat16* planes, int* ex, int* bad) {
+                                                            __nv_bfloat16* planes, int* ex, int* bad,
+                                                            const int* active) {
+  if (active && *active == 0) return;
   __shared__ double red[8];
   const int r = blockIdx.x;
   double mx = 0.0;
@@ -331,7 +337,8 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, con
 constexpr int OZ_CT = 32;
 
 __global__ void __launch_bounds__(256) oz_cols_exp_kernel(int R, int K, const double2* X, int64_t ldx, int conj,
-                                                          int mask, int* ex, int* bad) {
+                                                          int mask, int* ex, int* bad, const int* active) {
+  if (active && *active == 0) return;
   __shared__ double red[8][OZ_CT];
   const int j = blockIdx.x * OZ_CT + threadIdx.x;
   double mx = 0.0;
@@ -353,7 +360,9 @@ __global__ void __launch_bounds__(256) oz_cols_exp_kernel(int R, int K, const do
 
 __global__ void __launch_bounds__(256) oz_cols_digits_kernel(int R, int K, const double2* X, int64_t ldx, int conj,
                                                              int mask, int S, int npl, int rows_pad, int k_pad,
-                                                             __nv_bfloat16* planes, const int* ex) {
+                                                             __nv_bfloat16* planes, const int* ex,
+                                                             const int* active) {
+  if (active && *active == 0) return;
   __shared__ double2 tile[OZ_CT][OZ_CT + 1];   // [k][j]
   const int k0 = blockIdx.x * OZ_CT, j0 = blockIdx.y * OZ_CT;
   for (int i = threadIdx.y; i < OZ_CT; i += 8) {
@@ -424,7 +433,7 @@ bool oz_supported() {
 }
 
 cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
-                     int S, int npl, int* bad, cudaStream_t s, bool cols) {
+                     int S, int npl, int* bad, cudaStream_t s, bool cols, const int* active) {
   if (S < 1 || S > kOzSlicesMax || (npl != 2 && npl != 3)) return cudaErrorInvalidValue;
   op.rows = rows;
   op.K = K;
@@ -437,20 +446,21 @@ cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X
   if (rows == 0) return cudaSuccess;
   if (!cols) {
     oz_split_rows_kernel<<<op.rows_pad, 256, 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
-                                                     op.planes, op.ex, bad);
+                                                     op.planes, op.ex, bad, active);
     LAUNCH_NOTE(1);
   } else {
-    oz_cols_exp_kernel<<<(rows + OZ_CT - 1) / OZ_CT, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, op.ex, bad);
+    oz_cols_exp_kernel<<<(rows + OZ_CT - 1) / OZ_CT, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, op.ex, bad,
+                                                                             active);
     dim3 grid((op.k_pad + OZ_CT - 1) / OZ_CT, (op.rows_pad + OZ_CT - 1) / OZ_CT);
     oz_cols_digits_kernel<<<grid, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
-                                                          op.planes, op.ex);
+                                                          op.planes, op.ex, active);
     LAUNCH_NOTE(2);
   }
   return cudaGetLastError();
 }
 
 cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int* active) {
   if (A.K != B.K || A.S != B.S || A.npl != 2 || B.npl != 3 || A.k_pad != B.k_pad) return cudaErrorInvalidValue;
   // the integer sums of one level hold at most S products of 2^24 per K chunk
   if (A.k_pad > 15 * OZ_KCHUNK) return cudaErrorInvalidValue;
@@ -475,6 +485,7 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
   p.D = D;
   p.ldd = ldd;
   p.err = err;
+  p.active = active;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
@@ -482,8 +493,26 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
     attr = true;
   }
   dim3 grid(B.rows_pad / OZ_TN, 2 * p.mt);
+  void* kt0 = kt_enabled() ? kt_begin(s) : nullptr;
   oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(maps, p);
   LAUNCH_NOTE(1);
+  if (kt0) {
+    // algorithmic: the complex product over the K ranges the tiles process (8 flop per
+    // complex multiply-add); executed: the digit pairs' real products of the embedding
+    double alg = 0.0;
+    for (int mt = 0; mt < p.mt; ++mt)
+      for (int nt = 0; nt < B.rows_pad / OZ_TN; ++nt) {
+        const int m0 = mt * OZ_TM, n0 = nt * OZ_TN;
+        int klo = 0, khi = p.k_pad;
+        if (triA == 1) khi = std::min(khi, m0 + OZ_TM);
+        if (triB == 1) klo = std::max(klo, n0);
+        if (triB == 2) khi = std::min(khi, n0 + OZ_TN);
+        const int rows = std::min(OZ_TM, p.M - m0), cols = std::min(OZ_TN, p.N - n0);
+        if (khi > klo && rows > 0 && cols > 0) alg += 8.0 * rows * cols * (double)(khi - klo);
+      }
+    const double pairs = (double)p.S * (p.S + 1) / 2;
+    kt_end(kt0, 1, alg, alg * pairs, s);
+  }
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ __global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, i
   __shared__ double2 S[NB][NB + 1];
   __shared__ double2 X[NB][NB + 1];
   __shared__ double rdiag[NB];
+  __shared__ double pinv;   // 1 / pivot of the current column (one FP64 division per column)
   __shared__ int fail;
   if (*info != 0) return;
   const int tid = threadIdx.x;
@@ -39,12 +40,16 @@ __global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, i
         fail = 1;
         atomicCAS(info, 0, (int)(k0 + j + 1));
       } else {
-        S[j][j] = make_double2(sqrt(d), 0.0);
+        const double r = sqrt(d);
+        S[j][j] = make_double2(r, 0.0);
+        pinv = 1.0 / r;
       }
     }
     __syncthreads();
     if (fail) break;
-    double inv = 1.0 / S[j][j].x;
+    // FP64 division is an iterative sequence on the FP64 pipe (two FMAs per clock per SM
+    // here): one thread forms the reciprocal, the others read it
+    const double inv = pinv;
     for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] = zscale(S[i][j], inv);
     __syncthreads();
     // trailing update of the lower part: S[i][l] -= S[i][j] conj(S[l][j]), j < l <= i

@@ -229,10 +229,16 @@ void zgemm(const ZgemmArgs& in, double2* split_ws, size_t split_ws_elems, cudaSt
   p.ksplit = best_ks;
   int bm = best_b, bn = best_b;
   dim3 grid((p.N + bn - 1) / bn, (p.M + bm - 1) / bm, p.batch * p.ksplit);
+  void* kt0 = kt_enabled() ? kt_begin(s) : nullptr;
   if (bm == 64) zgemm_kernel<64, 64, 8, 4, 4><<<grid, 256, 0, s>>>(p, split_ws);
   else if (bm == 32) zgemm_kernel<32, 32, 8, 2, 2><<<grid, 256, 0, s>>>(p, split_ws);
   else zgemm_kernel<16, 16, 16, 1, 1><<<grid, 256, 0, s>>>(p, split_ws);
   LAUNCH_NOTE(1);
+  if (kt0) {
+    const int tb = p.maskB ? 1 : p.triB;
+    const double f = p.batch * tiled_product_flops(p.M, p.N, p.K, p.triA, tb, p.triD);
+    kt_end(kt0, 0, f, f, s);
+  }
   if (p.ksplit > 1) {
     int64_t total = (int64_t)p.M * p.N;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 4 * kSMs);

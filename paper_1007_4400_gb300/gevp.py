@@ -121,13 +121,16 @@ def load(build_if_missing: bool = True):
         L.gevp_assign_min_cost.argtypes = [i32, i32, C.POINTER(f64), C.POINTER(i64)]
         L.gevp_zgemm_emulated.argtypes = [vp, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp, i64, i32]
         L.gevp_reduce_emulated.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, C.POINTER(i64), i32]
+        L.gevp_kernel_timing.argtypes = [i32]
+        L.gevp_kernel_timing_read.argtypes = [C.POINTER(f64)]
         L.gevp_kernel_launches.argtypes = [vp]
         L.gevp_kernel_launches.restype = i64
         for name in ("gevp_create", "gevp_destroy", "gevp_set_stream", "gevp_reduce", "gevp_solve_sequence",
                      "gevp_solve_sequence_host", "gevp_solve_batched", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
                      "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_probe_peaks",
                      "gevp_matrix_variation", "gevp_deviation_angles", "gevp_assign_min_cost",
-                     "gevp_zgemm_emulated", "gevp_reduce_emulated"):
+                     "gevp_zgemm_emulated", "gevp_reduce_emulated", "gevp_kernel_timing",
+                     "gevp_kernel_timing_read"):
             getattr(L, name).restype = i32
         _LIB = L
         return L
@@ -492,6 +495,24 @@ def probe_peaks(device=None) -> dict:
     st = load().gevp_probe_peaks(h, out)
     _check(st, h)
     return {"fp64_fma_tflops": out[0], "fp64_dmma_tflops": out[1], "fp32_fma_tflops": out[2]}
+
+
+def kernel_timing(enable: bool) -> None:
+    """Start (clearing earlier records) or stop live timing of the GEMM kernels."""
+    st = load().gevp_kernel_timing(1 if enable else 0)
+    if st != 0:
+        raise GevpError(st, "gevp_kernel_timing")
+
+
+def kernel_timing_read() -> dict:
+    """Per kernel class: launches, total ms, algorithmic and executed flop."""
+    out = (C.c_double * 8)()
+    st = load().gevp_kernel_timing_read(out)
+    if st != 0:
+        raise GevpError(st, "gevp_kernel_timing_read")
+    names = ("zgemm_kernel", "oz_gemm_kernel")
+    return {names[c]: {"launches": int(out[4 * c]), "ms": out[4 * c + 1], "alg_flop": out[4 * c + 2],
+                       "exec_flop": out[4 * c + 3]} for c in range(2)}
 
 
 def kernel_launches(device=None) -> int:

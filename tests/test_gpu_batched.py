@@ -87,6 +87,22 @@ def test_graph_reuse_and_autotuner(cuda):
         assert np.abs(a - b).max() <= TOL_LAM * np.abs(a).max()
 
 
+def test_fp64_pipe_and_emulated_products_agree(cuda, orc):
+    """The same batch with the reduction and the rounds' W = C Q on the FP64 pipe
+    (reduce_slices 0) and emulated (8 digits), on one handle: the change of setting
+    rebuilds the plan and its captured round, and both match the oracle."""
+    seqs = _batch(SMALL[:4], 3, cuda)
+    r0 = _solve(seqs, "fp32", reduce_slices=0)
+    r8 = _solve(seqs, "fp32", reduce_slices=8)
+    r0b = _solve(seqs, "fp32", reduce_slices=0)
+    for r in (r0, r8, r0b):
+        assert r.status == 0 and r.stats["max_resid"] <= TOL_RES
+    for k, s in enumerate(seqs):
+        _check_kpoint(orc, s, r8.Lambda[k].cpu().numpy(), r8.resid[k].cpu().numpy(), r8.X[k].cpu().numpy())
+        a, b = r0.Lambda[k].cpu().numpy(), r0b.Lambda[k].cpu().numpy()
+        assert np.abs(a - b).max() <= TOL_LAM * np.abs(a).max()
+
+
 def test_keep_all_X_and_caller_start(cuda, orc):
     """Every step's eigenvectors (keep_all_X) and a caller-supplied start block for step 0."""
     seqs = _batch(SMALL[:2], 2, cuda)

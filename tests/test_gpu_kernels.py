@@ -70,7 +70,8 @@ def test_cholqr2_parity(cuda, orc, n, m):
     assert relmax(Rg, Rr) < 1e-10
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 17, 64, 140, 159, 161, 200, 301])
+# one CTA below 32, the eight-CTA cluster form for 32..256, the cooperative form above
+@pytest.mark.parametrize("m", [1, 2, 3, 17, 31, 32, 33, 64, 140, 159, 161, 200, 255, 256, 257, 301])
 def test_heev_small_parity(cuda, orc, m):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(400 + m)
