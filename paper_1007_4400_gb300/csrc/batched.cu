@@ -135,6 +135,13 @@ struct BatchPlan {
   char* oz_cq = nullptr;
   size_t oz_cq_bytes = 0;
   char* oz_qs = nullptr;   // the block's digits (inside oz_cq)
+  // the final check's X = L^-H Q, A X, B X: digits of every k-point's L^-H (rows) and B
+  // (rows), made once per call, and one k-point's A (per check)
+  std::vector<OzOperand> ozLH, ozBd;
+  OzOperand ozAd;
+  char* oz_fin = nullptr;
+  size_t oz_fin_bytes = 0;
+  char* oz_ad = nullptr;   // A's digits (inside oz_fin)
   int* oz_flags = nullptr;   // device: [0] kernel error code, [1] non-finite entry
   std::vector<cudaEvent_t> ev;
 };
@@ -146,6 +153,7 @@ void batch_release(BatchPlan* P) {
   if (P->arena) cudaFree(P->arena);
   if (P->oz_mem) cudaFree(P->oz_mem);
   if (P->oz_cq) cudaFree(P->oz_cq);
+  if (P->oz_fin) cudaFree(P->oz_fin);
   if (P->hD) cudaFreeHost(P->hD);
   for (auto e : P->ev) cudaEventDestroy(e);
   delete P;
@@ -798,6 +806,33 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
     }
     P->oz_qs = P->oz_cq + (cq - qs);
     P->ozC.assign(np, OzOperand{});
+    // L^-H and B digits for the final check, and room for one A
+    size_t fb = 256, ab = 0;
+    for (int k = 0; k < np; ++k) {
+      fb += 2 * oz_operand_bytes((int)n[k], (int)n[k], S, 2);
+      ab = std::max(ab, oz_operand_bytes((int)n[k], (int)n[k], S, 2));
+    }
+    fb += ab;
+    if (fb > P->oz_fin_bytes) {
+      if (P->oz_fin) cudaFree(P->oz_fin);
+      P->oz_fin = nullptr;
+      P->oz_fin_bytes = 0;
+      BCK(cudaMalloc(&P->oz_fin, fb));
+      P->oz_fin_bytes = fb;
+    }
+    P->ozLH.assign(np, OzOperand{});
+    P->ozBd.assign(np, OzOperand{});
+    char* f = P->oz_fin;
+    for (int k = 0; k < np; ++k) {
+      const BDesc& d = P->hD[k];
+      const int nk_ = (int)n[k];
+      // rows of L^-H (upper) = conjugated columns of L^-1
+      BCK(oz_split(P->ozLH[k], f, nk_, nk_, d.Linv, n[k], 1, 3, S, 2, P->oz_flags + 1, s, true));
+      f += oz_operand_bytes(nk_, nk_, S, 2);
+      BCK(oz_split(P->ozBd[k], f, nk_, nk_, (const double2*)B[k], ldb[k], 0, 0, S, 2, P->oz_flags + 1, s));
+      f += oz_operand_bytes(nk_, nk_, S, 2);
+    }
+    P->oz_ad = f;
   }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, evt(P, EV_T0), evt(P, EV_CHOL));
@@ -930,9 +965,24 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
       if (!any_active) {
         // ---- original-space check of the k-points that converged
         BCK(cudaEventRecord(evt(P, EV_FIN0), s));
-        launch(P, P->c_xf, s, tune);
-        launch(P, P->c_ax, s, tune);
-        launch(P, P->c_bx, s, tune);
+        if (P->oz_S > 0 && (int)P->ozLH.size() == np) {
+          // emulated per k-point; launches of k-points without a pending check do nothing
+          const int S = P->oz_S;
+          for (int k = 0; k < np; ++k) {
+            const BDesc& d = P->hD[k];
+            const int* fin = d.flags + 12;
+            BCK(oz_split(P->ozQ, P->oz_qs, d.nev, d.n, d.Q, d.m, 0, 0, S, 3, P->oz_flags + 1, s, true, fin));
+            BCK(oz_gemm(P->ozLH[k], P->ozQ, 2, 0, d.Xf, d.m, P->oz_flags, s, fin));
+            BCK(oz_split(P->ozAd, P->oz_ad, d.n, d.n, d.A, d.lda, 0, 0, S, 2, P->oz_flags + 1, s, false, fin));
+            BCK(oz_split(P->ozQ, P->oz_qs, d.nev, d.n, d.Xf, d.m, 0, 0, S, 3, P->oz_flags + 1, s, true, fin));
+            BCK(oz_gemm(P->ozAd, P->ozQ, 0, 0, d.Y1, d.m, P->oz_flags, s, fin));
+            BCK(oz_gemm(P->ozBd[k], P->ozQ, 0, 0, d.Y2, d.m, P->oz_flags, s, fin));
+          }
+        } else {
+          launch(P, P->c_xf, s, tune);
+          launch(P, P->c_ax, s, tune);
+          launch(P, P->c_bx, s, tune);
+        }
         bk_final_check(P->dD, np, P->nevmax, s);
         bk_final_status(P->dD, np, P->dStatus, s);
         BCK(cudaMemcpyAsync(P->hStatus, P->dStatus, np * sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -67,7 +67,8 @@ struct gevp_ctx {
   gevp::OzOperand ozLA, ozLB, ozAB[2], ozTA[2];
   // solver products on the main stream: C (rows, per problem), A (rows, per final check),
   // B (rows, kept while the factorisation is), the block (columns, per product)
-  gevp::OzOperand ozC, ozA, ozB, ozQ;
+  gevp::OzOperand ozC, ozA, ozB, ozQ, ozLH;
+  int64_t ozLH_gen = -1;                    // chol_gen the L^-H rows (ozLH) were split from
   const void* ozC_src = nullptr;            // the C whose digits ozC holds (null: none)
   const void* ozB_src = nullptr;            // the B whose digits ozB holds, for chol_gen ozB_gen
   int64_t ozB_gen = -1;
@@ -356,6 +357,7 @@ gevp_status oz_reserve(gevp_ctx* h, int side, size_t need) {
     h->oz_l_gen = -1;
     h->ozC_src = nullptr;
     h->ozB_src = nullptr;
+    h->ozLH_gen = -1;
   }
   void* p = nullptr;
   CK(cudaMalloc(&p, need));
@@ -364,17 +366,19 @@ gevp_status oz_reserve(gevp_ctx* h, int side, size_t need) {
   return GEVP_OK;
 }
 
-// Main-stream digit scratch: [L^-1 rows | L^-H columns | reduction: tril(A) | T | A | B]
+// Main-stream digit scratch: [L^-1 rows | L^-H columns | reduction: tril(A) | T | A | B |
+// L^-H rows (the back-transform's left operand)]
 // (the solver's C digits reuse the T region and the block's digits the tril(A) region:
 // the reduction of a problem is finished before its solve starts, on the same stream)
 size_t oz_main_bytes(int64_t n, int S) {
   const size_t bA = gevp::oz_operand_bytes((int)n, (int)n, S, 2), bB = gevp::oz_operand_bytes((int)n, (int)n, S, 3);
-  return 4 * bA + 2 * bB;
+  return 5 * bA + 2 * bB;
 }
-char* oz_region(gevp_ctx* h, int64_t n, int which) {   // 0 L^-1, 1 L^-H, 2 tril(A)/block, 3 T/C, 4 A, 5 B
+// 0 L^-1, 1 L^-H columns, 2 tril(A)/block, 3 T/C, 4 A, 5 B, 6 L^-H rows
+char* oz_region(gevp_ctx* h, int64_t n, int which) {
   const int S = h->oz_slices;
   const size_t bA = gevp::oz_operand_bytes((int)n, (int)n, S, 2), bB = gevp::oz_operand_bytes((int)n, (int)n, S, 3);
-  const size_t off[6] = {0, bA, bA + bB, bA + 2 * bB, 2 * bA + 2 * bB, 3 * bA + 2 * bB};
+  const size_t off[7] = {0, bA, bA + bB, bA + 2 * bB, 2 * bA + 2 * bB, 3 * bA + 2 * bB, 4 * bA + 2 * bB};
   return h->ozmem[0] + off[which];
 }
 
@@ -739,9 +743,22 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     }
     if (S.nlock >= nev) {
       // ---- final check in the original space
-      ZgemmArgs x = zg((int)n, nev, (int)n, h->Linv, n, 1, h->Q, ld, 0, h->Xf, ld);
-      x.triA = 2;
-      zgemm(x, h->split, h->split_elems, h->stream);
+      if (oz) {
+        // X = L^-H Q: the rows of L^-H (upper) are the conjugated columns of L^-1, made
+        // once per factorisation
+        if (h->ozLH_gen != h->chol_gen || h->ozLH.S != h->oz_slices) {
+          CK(gevp::oz_split(h->ozLH, oz_region(h, n, 6), (int)n, (int)n, h->Linv, n, 1, 3, h->oz_slices, 2,
+                            h->ozflags + 1, h->stream, true));
+          h->ozLH_gen = h->chol_gen;
+        }
+        CK(gevp::oz_split(h->ozQ, oz_region(h, n, 2), nev, (int)n, h->Q, ld, 0, 0, h->oz_slices, 3, h->ozflags + 1,
+                          h->stream, true));
+        CK(gevp::oz_gemm(h->ozLH, h->ozQ, 2, 0, h->Xf, ld, h->ozflags, h->stream));
+      } else {
+        ZgemmArgs x = zg((int)n, nev, (int)n, h->Linv, n, 1, h->Q, ld, 0, h->Xf, ld);
+        x.triA = 2;
+        zgemm(x, h->split, h->split_elems, h->stream);
+      }
       if (oz) {
         // A X and B X emulated: A's digits once per problem, B's while it stays factorised
         if (!oz_a_ready) {

@@ -61,7 +61,7 @@ struct OzParams {
   int mt;          // 128-row tiles of one part
   int k_pad;       // padded K (multiple of 64)
   int S;           // digits per entry
-  int triA;        // 1: op(A)[i][k] = 0 for k > i
+  int triA;        // 1: op(A)[i][k] = 0 for k > i;  2: op(A)[i][k] = 0 for k < i
   int triB;        // 1: op(B)[k][j] = 0 for k < j;  2: op(B)[k][j] = 0 for k > j
   const int* ea;   // row exponents of op(A)
   const int* eb;   // column exponents of op(B)
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   // K range of the tile from the triangular structure, in whole 64-blocks
   int klo = 0, khi = p.k_pad;
   if (p.triA == 1) khi = min(khi, m0 + OZ_TM);
+  if (p.triA == 2) klo = max(klo, m0);
   if (p.triB == 1) klo = max(klo, n0);
   if (p.triB == 2) khi = min(khi, n0 + OZ_TN);
   const int klen = max(0, khi - klo);
@@ -336,15 +337,22 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, con
 // staged in shared memory and written out transposed, so the digit stores run along k.
 constexpr int OZ_CT = 32;
 
+// ex[j] starts at kExpNone; each block (32 columns x one slice of rows) raises it to the
+// exponent of its slice's largest entry (the exponent of a maximum is the maximum of the
+// exponents); a column with no nonzero entry keeps kExpNone, read as 0.
+constexpr int kExpNone = (int)0x80808080;   // the cudaMemset byte pattern 0x80
+constexpr int OZ_CE_ROWS = 256;             // rows per slice
+
 __global__ void __launch_bounds__(256) oz_cols_exp_kernel(int R, int K, const double2* X, int64_t ldx, int conj,
                                                           int mask, int* ex, int* bad, const int* active) {
   if (active && *active == 0) return;
   __shared__ double red[8][OZ_CT];
   const int j = blockIdx.x * OZ_CT + threadIdx.x;
+  const int k0 = blockIdx.y * OZ_CE_ROWS, k1 = min(K, k0 + OZ_CE_ROWS);
   double mx = 0.0;
   bool nonfinite = false;
   if (j < R)
-    for (int k = threadIdx.y; k < K; k += 8) {
+    for (int k = k0 + threadIdx.y; k < k1; k += 8) {
       const double2 v = oz_masked(X[(int64_t)k * ldx + j], j, k, conj, mask);
       if (!oz_finite(v)) nonfinite = true;
       else mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(256) oz_cols_exp_kernel(int R, int K, const do
   __syncthreads();
   if (threadIdx.y == 0 && j < R) {
     for (int t = 1; t < 8; ++t) mx = fmax(mx, red[t][threadIdx.x]);
-    ex[j] = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (mx > 0.0) atomicMax(&ex[j], ilogb(mx) + 2);
   }
 }
 
@@ -379,12 +387,20 @@ __global__ void __launch_bounds__(256) oz_cols_digits_kernel(int R, int K, const
     const int j = j0 + jj;
     if (j >= rows_pad) break;
     const double2 v = tile[threadIdx.x][jj];
-    const int shift = 7 * S - (j < R ? ex[j] : 0);
+    const int e = j < R ? ex[j] : 0;
+    const int shift = 7 * S - (e == kExpNone ? 0 : e);
     const size_t o = (size_t)j * k_pad + k;
     oz_digits(v.x, shift, S, planes + o, plane);
     oz_digits(v.y, shift, S, planes + pstride + o, plane);
     if (npl == 3) oz_digits(-v.y, shift, S, planes + 2 * pstride + o, plane);
   }
+}
+
+// columns with no nonzero entry: exponent 0 (the product kernel scales by 2^(e_i + f_j))
+__global__ void oz_exp_fix_kernel(int R, int* ex, const int* active) {
+  if (active && *active == 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < R && ex[j] == kExpNone) ex[j] = 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -449,12 +465,14 @@ cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X
                                                      op.planes, op.ex, bad, active);
     LAUNCH_NOTE(1);
   } else {
-    oz_cols_exp_kernel<<<(rows + OZ_CT - 1) / OZ_CT, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, op.ex, bad,
-                                                                             active);
+    cudaMemsetAsync(op.ex, 0x80, (size_t)rows * sizeof(int), s);
+    dim3 egrid((rows + OZ_CT - 1) / OZ_CT, std::max(1, (K + OZ_CE_ROWS - 1) / OZ_CE_ROWS));
+    oz_cols_exp_kernel<<<egrid, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, op.ex, bad, active);
     dim3 grid((op.k_pad + OZ_CT - 1) / OZ_CT, (op.rows_pad + OZ_CT - 1) / OZ_CT);
     oz_cols_digits_kernel<<<grid, dim3(OZ_CT, 8), 0, s>>>(rows, K, X, ldx, conj, mask, S, npl, op.rows_pad, op.k_pad,
                                                           op.planes, op.ex, active);
-    LAUNCH_NOTE(2);
+    oz_exp_fix_kernel<<<(rows + 255) / 256, 256, 0, s>>>(rows, op.ex, active);
+    LAUNCH_NOTE(3);
   }
   return cudaGetLastError();
 }
@@ -505,6 +523,7 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
         const int m0 = mt * OZ_TM, n0 = nt * OZ_TN;
         int klo = 0, khi = p.k_pad;
         if (triA == 1) khi = std::min(khi, m0 + OZ_TM);
+        if (triA == 2) klo = std::max(klo, m0);
         if (triB == 1) klo = std::max(klo, n0);
         if (triB == 2) khi = std::min(khi, n0 + OZ_TN);
         const int rows = std::min(OZ_TM, p.M - m0), cols = std::min(OZ_TN, p.N - n0);
