@@ -480,22 +480,60 @@ __device__ double block_sum_d(double v, double* red) {
 
 // Ogita-Aishima: lam_i = Re S_ii / (1 - Re R_ii); delta = 2 (||S - diag(lam)||_F + ||G||_F ||R||_F).
 // scal[0] = delta, scal[1] = ||G||_F (input, computed once).
-__global__ void oa_scalars_kernel(int m, const double2* R, const double2* S, double* lam, double* scal) {
+// The same scalars over many CTAs (one SM retires about two FP64 FMAs per clock, so the
+// m^2 sums of one CTA take tens of microseconds): per-block partial sums, then one thread
+// adds them in block order (deterministic). lam is written by the diagonal's owners.
+__global__ void __launch_bounds__(256) oa_partial_kernel(int m, const double2* R, const double2* S, double* lam,
+                                                         double* part) {
   __shared__ double red[32];
   double soff = 0.0, r2 = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x)
-    lam[i] = S[i * m + i].x / (1.0 - R[i * m + i].x);
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e / m, j = e % m;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mm; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e % m);
     double2 sv = S[e];
-    if (i == j) sv.x -= lam[i];
+    const double2 rv = R[e];
+    if (i == j) {
+      const double li = sv.x / (1.0 - rv.x);
+      lam[i] = li;
+      sv.x -= li;
+    }
     soff += zabs2(sv);
-    r2 += zabs2(R[e]);
+    r2 += zabs2(rv);
   }
   soff = block_sum_d(soff, red);
   r2 = block_sum_d(r2, red);
-  if (threadIdx.x == 0) scal[0] = 2.0 * (sqrt(soff) + scal[1] * sqrt(r2));
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = soff;
+    part[2 * blockIdx.x + 1] = r2;
+  }
+}
+
+__global__ void oa_finish_kernel(int nblk, const double* part, double* scal) {
+  if (threadIdx.x != 0) return;
+  double soff = 0.0, r2 = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    soff += part[2 * b];
+    r2 += part[2 * b + 1];
+  }
+  scal[0] = 2.0 * (sqrt(soff) + scal[1] * sqrt(r2));
+}
+
+// ||G||_F over many CTAs: per-block partial sums of |g|^2, then out = sqrt(sum) in block order
+__global__ void __launch_bounds__(256) frob_partial_kernel(int m, const double2* G, int64_t ldg, double* part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mm; e += (int64_t)gridDim.x * blockDim.x)
+    s += zabs2(G[(e / m) * ldg + (e % m)]);
+  s = block_sum_d(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void frob_finish_kernel(int nblk, const double* part, double* out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[b];
+  out[0] = sqrt(s);
 }
 
 __global__ void oa_update_kernel(int m, const double2* R, const double2* S, const double* lam, const double* scal,
@@ -519,13 +557,6 @@ __global__ void oa_update_kernel(int m, const double2* R, const double2* S, cons
   }
 }
 
-__global__ void frob_kernel(int m, const double2* G, int64_t ldg, double* out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) s += zabs2(G[(e / m) * ldg + (e % m)]);
-  s = block_sum_d(s, red);
-  if (threadIdx.x == 0) out[0] = sqrt(s);
-}
 
 // Clusters the refinement leaves mixed (pairs closer than its threshold): S = Z^H G Z is
 // diagonal apart from those couplings. One CTA finds the pairs with |s_pq| above tol and
@@ -748,8 +779,12 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   }
   gather_z_kernel<<<blocks, 256, 0, s>>>(m, w.Z32, w.perm, w.Z, m);
   LAUNCH_NOTE(1);
-  frob_kernel<<<1, 1024, 0, s>>>(m, G, ldg, w.scal + 1);
-  LAUNCH_NOTE(1);
+  // partial sums in E (free until the refinement's first product writes it)
+  const int nblk = (int)std::min<int64_t>(64, std::max<int64_t>(1, ((int64_t)m * m + 255) / 256));
+  double* part = (double*)w.E;
+  frob_partial_kernel<<<nblk, 256, 0, s>>>(m, G, ldg, part);
+  frob_finish_kernel<<<1, 32, 0, s>>>(nblk, part, w.scal + 1);
+  LAUNCH_NOTE(2);
   double2* Z = w.Z;
   double2* Zn = w.T;   // ping-pong partner
   for (int it = 0; it <= refine_iters; ++it) {
@@ -763,8 +798,10 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
     zgemm(b, w.split_ws, w.split_ws_elems, s);
     ZgemmArgs c = zg(m, m, m, Z, m, 1, w.E, m, 0, w.S, m);
     zgemm(c, w.split_ws, w.split_ws_elems, s);
-    oa_scalars_kernel<<<1, 1024, 0, s>>>(m, w.R, w.S, w.lam, w.scal);
-    LAUNCH_NOTE(1);
+    // partial sums in E: the product G Z it held has been consumed by S = Z^H (G Z)
+    oa_partial_kernel<<<nblk, 256, 0, s>>>(m, w.R, w.S, w.lam, part);
+    oa_finish_kernel<<<1, 32, 0, s>>>(nblk, part, w.scal);
+    LAUNCH_NOTE(2);
     // the last step corrects only the orthonormality (E = R/2 everywhere: a symmetric
     // Newton-Schulz step) and yields Rayleigh quotients of the vectors it returns
     oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, it == refine_iters ? 1 : 0);
