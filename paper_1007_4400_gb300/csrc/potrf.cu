@@ -40,9 +40,10 @@ __global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, i
         fail = 1;
         atomicCAS(info, 0, (int)(k0 + j + 1));
       } else {
-        const double r = sqrt(d);
-        S[j][j] = make_double2(r, 0.0);
-        pinv = 1.0 / r;
+        // one reciprocal square root, then the root as d * rsqrt(d)
+        const double ri = rsqrt(d);
+        S[j][j] = make_double2(d * ri, 0.0);
+        pinv = ri;
       }
     }
     __syncthreads();
@@ -69,18 +70,26 @@ __global__ void potrf_diag_kernel(double2* A, int64_t lda, int kb, int64_t k0, i
     A[i * lda + j] = (j <= i) ? S[i][j] : make_double2(0.0, 0.0);
   }
   if (fail) return;
-  // inverse: row i of X = S^-1 from rows < i, all columns c <= i in parallel
+  // inverse: row i of X = S^-1 from rows < i: X[i][i] = 1 / s_ii and, for c < i,
+  // X[i][c] = -(1 / s_ii) sum_{k=c}^{i-1} S[i][k] X[k][c]. One warp per column, the lanes
+  // splitting the sum: a product and a five-level shuffle reduction instead of a chain of
+  // up to kb dependent FP64 operations per thread (the block otherwise waits at barriers)
   for (int j = tid; j < kb; j += blockDim.x) rdiag[j] = 1.0 / S[j][j].x;
   __syncthreads();
+  const int lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
   for (int i = 0; i < kb; ++i) {
-    for (int c = tid; c <= i; c += blockDim.x) {
-      double2 v = make_double2(c == i ? 1.0 : 0.0, 0.0);
-      for (int k = c; k < i; ++k) {
+    for (int c = wid; c <= i; c += nw) {
+      double sx = 0.0, sy = 0.0;
+      for (int k = c + lane; k < i; k += 32) {
         const double2 l = S[i][k], x = X[k][c];
-        v.x -= l.x * x.x - l.y * x.y;
-        v.y -= l.x * x.y + l.y * x.x;
+        sx = fma(l.x, x.x, fma(-l.y, x.y, sx));
+        sy = fma(l.x, x.y, fma(l.y, x.x, sy));
       }
-      X[i][c] = zscale(v, rdiag[i]);
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) X[i][c] = c == i ? make_double2(rdiag[i], 0.0) : make_double2(-rdiag[i] * sx, -rdiag[i] * sy);
     }
     __syncthreads();
   }
@@ -178,7 +187,7 @@ void potrf_lower(int64_t n, double2* A, int64_t lda, int* info_dev, double2* Lin
     int kb = (int)std::min<int64_t>(NB, n - k0);
     double2* Akk = A + k0 * lda + k0;
     double2* Likk = Linv + k0 * ldi + k0;
-    potrf_diag_kernel<<<1, 256, 0, s>>>(Akk, lda, kb, k0, info_dev, Likk, ldi);
+    potrf_diag_kernel<<<1, 1024, 0, s>>>(Akk, lda, kb, k0, info_dev, Likk, ldi);
     LAUNCH_NOTE(1);
     int64_t rem = n - k0 - kb;
     if (rem <= 0) break;
