@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--seq-steps", type=int, default=10, help="kpoint_batch workload: problems per k-point")
     p.add_argument("--reduce-slices", type=int, default=8,
                    help="digits of the emulated FP64 products of the reduction (0: FP64 pipe)")
-    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki"], default=None,
+    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki", "seq_small"],
+                   default=None,
                    help="run only a few launches of one kernel (n 2048, m 140) for ncu captures")
     return p.parse_args()
 
@@ -82,6 +83,14 @@ def kernel_case(args):
         print(json.dumps({"kernel_case": "variation", "n": n, "ms": ms, "alg_bytes": alg,
                           "GBps": alg / (ms * 1e-3) / 1e9, "bytes_moved": 48.0 * n * n,
                           "fp64_ops": 5.0 * n * n, "delta": d, "counts": c}))
+        return 0
+    if args.kernel_case == "seq_small":
+        # a short sequence (3 problems, n 1024, nev 64, nex 24, FP32-class filter) for
+        # captures of the small dense kernels (Cholesky blocks, Jacobi, refinement)
+        seq = synth.make_sequence(1, 1024, 3, 64, 24, device="cpu")
+        r = gevp.solve_sequence([a.to(dev) for a in seq.A], seq.B.to(dev), 64, nex=24, filter_prec="fp32")
+        torch.cuda.synchronize()
+        print(f"kernel case seq_small done: status {r.status}, max residual {float(r.resid.max()):.2e}")
         return 0
     if args.kernel_case == "ozaki":
         # the emulated FP64 product D = A B^H (n = 2048, 8 digits) and the reduction to
