@@ -52,3 +52,23 @@ def test_binding_rejects_cpu_tensors():
     A = torch.eye(4, dtype=torch.complex128)
     with pytest.raises(TypeError):
         gevp.reduce(A, A)
+
+
+def test_kernel_timing_records_nothing_without_launches():
+    # the live GEMM timing is host bookkeeping around launches: enabling, reading and
+    # disabling it needs no device, and with no launch every counter is zero
+    from paper_1007_4400_gb300 import gevp
+    gevp.kernel_timing(True)
+    out = gevp.kernel_timing_read()
+    gevp.kernel_timing(False)
+    assert set(out) == {"zgemm_kernel", "oz_gemm_kernel"}
+    for v in out.values():
+        assert v["launches"] == 0 and v["ms"] == 0.0 and v["alg_flop"] == 0.0 and v["exec_flop"] == 0.0
+
+
+def test_defaults_select_the_emulated_products():
+    from paper_1007_4400_gb300 import gevp
+    o = gevp.default_opts()
+    assert o.reduce_slices == 8 and o.refresh_window == 0 and o.deg_max == 48
+    with pytest.raises(KeyError):
+        gevp.default_opts(no_such_option=1)
