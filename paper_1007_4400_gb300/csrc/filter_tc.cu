@@ -109,7 +109,8 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* amaps, const CUtensor
   const uint32_t tmem = tmem_sh;
 
   if (warp == 0 && lane == 0) {
-    for (int i = 0; i < niter; ++i) {
+    int issued = 0;
+    for (int i = 0; i < niter; ++i, issued = i) {
       int s = i % STAGES;
       uint32_t ph = (uint32_t)(i / STAGES) & 1u;
       if (i >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, p.err, 1)) break;
@@ -125,6 +126,10 @@ __device__ __forceinline__ void tc_tile(const CUtensorMap* amaps, const CUtensor
       tma_load_2d(tile(s, 4), B + 1, kx, c0, &full[s]);
       tma_load_2d(tile(s, 5), B + 2, kx, c0, &full[s]);
     }
+    // every copy issued has landed before the CTA leaves (bounded; immediate unless a wait
+    // elsewhere gave up)
+    for (int i = max(0, issued - STAGES); i < issued; ++i)
+      mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u, p.err, 4);
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16(TM, p.nchunk);
     for (int i = 0; i < niter; ++i) {

@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         tma_load_3d(sa_tile + OZ_TILE_BYTES, &maps.b[pb], kx, n0, tb, &full[st]);
       }
     }
+    // every copy issued has landed before the CTA leaves (normally they were all consumed;
+    // after a wait elsewhere gave up they may still be in flight): bounded waits on the
+    // last issue of every stage
+    for (int i = max(0, it - OZ_ST); i < it; ++i) mbar_wait(&full[i % OZ_ST], (uint32_t)(i / OZ_ST) & 1u, p.err, 25);
   } else if (warp == OZ_EPI_WARPS + 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16(OZ_TM, OZ_TN);
     int it = 0;
