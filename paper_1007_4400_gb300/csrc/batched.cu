@@ -142,6 +142,8 @@ struct BatchPlan {
   char* oz_fin = nullptr;
   size_t oz_fin_bytes = 0;
   char* oz_ad = nullptr;   // A's digits (inside oz_fin)
+  double* oz_ws = nullptr;  // split-K partials of one k-point's thin product
+  size_t oz_ws_doubles = 0;
   int* oz_flags = nullptr;   // device: [0] kernel error code, [1] non-finite entry
   std::vector<cudaEvent_t> ev;
 };
@@ -154,6 +156,7 @@ void batch_release(BatchPlan* P) {
   if (P->oz_mem) cudaFree(P->oz_mem);
   if (P->oz_cq) cudaFree(P->oz_cq);
   if (P->oz_fin) cudaFree(P->oz_fin);
+  if (P->oz_ws) cudaFree(P->oz_ws);
   if (P->hD) cudaFreeHost(P->hD);
   for (auto e : P->ev) cudaEventDestroy(e);
   delete P;
@@ -519,7 +522,7 @@ void enqueue_rr(BatchPlan* P, cudaStream_t s, bool tune) {
     for (int k = 0; k < np; ++k) {
       const BDesc& d = P->hD[k];
       oz_split(P->ozQ, P->oz_qs, d.m, d.n, d.Q, d.m, 0, 0, P->oz_S, 3, P->oz_flags + 1, s, true, d.flags);
-      oz_gemm(P->ozC[k], P->ozQ, 0, 0, d.Wt, d.m, P->oz_flags, s, d.flags);
+      oz_gemm(P->ozC[k], P->ozQ, 0, 0, d.Wt, d.m, P->oz_flags, s, d.flags, P->oz_ws, P->oz_ws_doubles);
     }
   } else {
     launch(P, P->c_wt, s, tune);
@@ -833,6 +836,15 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
       f += oz_operand_bytes(nk_, nk_, S, 2);
     }
     P->oz_ad = f;
+    size_t wd = 0;
+    for (int k = 0; k < np; ++k) wd = std::max(wd, oz_split_k_doubles((int)n[k], P->hD[k].m));
+    if (wd > P->oz_ws_doubles) {
+      if (P->oz_ws) cudaFree(P->oz_ws);
+      P->oz_ws = nullptr;
+      P->oz_ws_doubles = 0;
+      BCK(cudaMalloc(&P->oz_ws, wd * sizeof(double)));
+      P->oz_ws_doubles = wd;
+    }
   }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, evt(P, EV_T0), evt(P, EV_CHOL));
@@ -972,11 +984,11 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
             const BDesc& d = P->hD[k];
             const int* fin = d.flags + 12;
             BCK(oz_split(P->ozQ, P->oz_qs, d.nev, d.n, d.Q, d.m, 0, 0, S, 3, P->oz_flags + 1, s, true, fin));
-            BCK(oz_gemm(P->ozLH[k], P->ozQ, 2, 0, d.Xf, d.m, P->oz_flags, s, fin));
+            BCK(oz_gemm(P->ozLH[k], P->ozQ, 2, 0, d.Xf, d.m, P->oz_flags, s, fin, P->oz_ws, P->oz_ws_doubles));
             BCK(oz_split(P->ozAd, P->oz_ad, d.n, d.n, d.A, d.lda, 0, 0, S, 2, P->oz_flags + 1, s, false, fin));
             BCK(oz_split(P->ozQ, P->oz_qs, d.nev, d.n, d.Xf, d.m, 0, 0, S, 3, P->oz_flags + 1, s, true, fin));
-            BCK(oz_gemm(P->ozAd, P->ozQ, 0, 0, d.Y1, d.m, P->oz_flags, s, fin));
-            BCK(oz_gemm(P->ozBd[k], P->ozQ, 0, 0, d.Y2, d.m, P->oz_flags, s, fin));
+            BCK(oz_gemm(P->ozAd, P->ozQ, 0, 0, d.Y1, d.m, P->oz_flags, s, fin, P->oz_ws, P->oz_ws_doubles));
+            BCK(oz_gemm(P->ozBd[k], P->ozQ, 0, 0, d.Y2, d.m, P->oz_flags, s, fin, P->oz_ws, P->oz_ws_doubles));
           }
         } else {
           launch(P, P->c_xf, s, tune);

@@ -69,6 +69,8 @@ struct gevp_ctx {
   // B (rows, kept while the factorisation is), the block (columns, per product)
   gevp::OzOperand ozC, ozA, ozB, ozQ, ozLH;
   int64_t ozLH_gen = -1;                    // chol_gen the L^-H rows (ozLH) were split from
+  double* ozws = nullptr;                   // split-K partials of the thin emulated products
+  size_t ozws_doubles = 0;
   const void* ozC_src = nullptr;            // the C whose digits ozC holds (null: none)
   const void* ozB_src = nullptr;            // the B whose digits ozB holds, for chol_gen ozB_gen
   int64_t ozB_gen = -1;
@@ -388,7 +390,7 @@ gevp_status oz_times_block(gevp_ctx* h, const gevp::OzOperand& M, int64_t n, int
                            int64_t ldx, double2* D, int64_t ldd) {
   CK(gevp::oz_split(h->ozQ, oz_region(h, n, 2), ncols, (int)n, X, ldx, 0, 0, h->oz_slices, 3, h->ozflags + 1,
                     h->stream, true));
-  CK(gevp::oz_gemm(M, h->ozQ, 0, 0, D, ldd, h->ozflags, h->stream));
+  CK(gevp::oz_gemm(M, h->ozQ, 0, 0, D, ldd, h->ozflags, h->stream, nullptr, h->ozws, h->ozws_doubles));
   return GEVP_OK;
 }
 
@@ -717,6 +719,20 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     CK(gevp::oz_split(h->ozC, oz_region(h, n, 3), (int)n, (int)n, h->C, n, 0, 0, h->oz_slices, 2, h->ozflags + 1,
                       h->stream));
     h->ozC_src = h->C;
+    // split-K partials of the n x m products (W = C Q, the back-transform, A X, B X)
+    const size_t wd = gevp::oz_split_k_doubles((int)n, m);
+    if (wd > h->ozws_doubles) {
+      if (h->ozws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ozws);
+      }
+      h->ozws = nullptr;
+      h->ozws_doubles = 0;
+      void* p = nullptr;
+      CK(cudaMalloc(&p, wd * sizeof(double)));
+      h->ozws = (double*)p;
+      h->ozws_doubles = wd;
+    }
   }
   tm.mark(PH_BOUNDS);
   if (!warm) {
@@ -753,7 +769,7 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
         }
         CK(gevp::oz_split(h->ozQ, oz_region(h, n, 2), nev, (int)n, h->Q, ld, 0, 0, h->oz_slices, 3, h->ozflags + 1,
                           h->stream, true));
-        CK(gevp::oz_gemm(h->ozLH, h->ozQ, 2, 0, h->Xf, ld, h->ozflags, h->stream));
+        CK(gevp::oz_gemm(h->ozLH, h->ozQ, 2, 0, h->Xf, ld, h->ozflags, h->stream, nullptr, h->ozws, h->ozws_doubles));
       } else {
         ZgemmArgs x = zg((int)n, nev, (int)n, h->Linv, n, 1, h->Q, ld, 0, h->Xf, ld);
         x.triA = 2;
@@ -774,8 +790,8 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
         }
         CK(gevp::oz_split(h->ozQ, oz_region(h, n, 2), nev, (int)n, h->Xf, ld, 0, 0, h->oz_slices, 3, h->ozflags + 1,
                           h->stream, true));
-        CK(gevp::oz_gemm(h->ozA, h->ozQ, 0, 0, h->Y1, ld, h->ozflags, h->stream));
-        CK(gevp::oz_gemm(h->ozB, h->ozQ, 0, 0, h->Y2, ld, h->ozflags, h->stream));
+        CK(gevp::oz_gemm(h->ozA, h->ozQ, 0, 0, h->Y1, ld, h->ozflags, h->stream, nullptr, h->ozws, h->ozws_doubles));
+        CK(gevp::oz_gemm(h->ozB, h->ozQ, 0, 0, h->Y2, ld, h->ozflags, h->stream, nullptr, h->ozws, h->ozws_doubles));
       } else {
         ZgemmArgs ax = zg((int)n, nev, (int)n, A, lda, 0, h->Xf, ld, 0, h->Y1, ld);
         zgemm(ax, h->split, h->split_elems, h->stream);
@@ -1019,6 +1035,7 @@ gevp_status gevp_destroy(gevp_handle h) {
   for (int i = 0; i < 2; ++i)
     if (h->ozmem[i]) cudaFree(h->ozmem[i]);
   if (h->ozflags) cudaFree(h->ozflags);
+  if (h->ozws) cudaFree(h->ozws);
   if (h->hb2) cudaFreeHost(h->hb2);
   for (cudaEvent_t e : {h->ev_main, h->ev_side, h->ev_user})
     if (e) cudaEventDestroy(e);

@@ -279,8 +279,12 @@ bool oz_supported();
 cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
                      int S, int npl, int* bad, cudaStream_t s, bool cols = false, const int* active = nullptr);
 // D (A.rows x B.rows) = op(A) op(B); triA 1: op(A) lower; triB 1: op(B) lower, 2: upper
+// ws (nullable, ws_doubles >= oz_split_k_doubles(M, N)): when the grid would leave SMs
+// idle, K is cut into up to kOzSplitKMax slices whose FP64 partials are summed in slice order
+constexpr int kOzSplitKMax = 8;
+size_t oz_split_k_doubles(int M, int N);
 cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
-                    cudaStream_t s, const int* active = nullptr);
+                    cudaStream_t s, const int* active = nullptr, double* ws = nullptr, size_t ws_doubles = 0);
 
 // ---------------------------------------------------------------- deviation angles
 // slices of the column-norm reduction (part needs slices * k doubles)

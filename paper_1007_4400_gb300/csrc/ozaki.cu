@@ -69,6 +69,8 @@ struct OzParams {
   int64_t ldd;
   int* err;
   const int* active;   // nullable device flag: 0 = skip the whole launch (a converged problem)
+  double* ws;          // split K: this slice's partial, [z][part][M][N] (null: write D)
+  int kspan;           // split K: the K range of one slice (a multiple of 64)
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
@@ -90,6 +92,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   if (p.triA == 2) klo = max(klo, m0);
   if (p.triB == 1) klo = max(klo, n0);
   if (p.triB == 2) khi = min(khi, n0 + OZ_TN);
+  if (p.ws) {   // split K: this CTA's slice
+    klo = max(klo, (int)blockIdx.z * p.kspan);
+    khi = min(khi, ((int)blockIdx.z + 1) * p.kspan);
+  }
   const int klen = max(0, khi - klo);
   const int nchunk = (klen + OZ_KCHUNK - 1) / OZ_KCHUNK;
   const int npairs = p.S * (p.S + 1) / 2;
@@ -194,7 +200,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     const int row = m0 + q * 32 + lane;
     const bool row_ok = row < p.M;
     const int er = row_ok ? p.ea[row] : 0;
-    double* Dd = (double*)p.D;
+    // output: interleaved complex D (double 2 (row ldd + col) + part), or this slice's
+    // partial (double row N + col of plane (z, part) of the workspace)
+    double* Dd = p.ws ? p.ws + ((size_t)blockIdx.z * 2 + part) * (size_t)p.M * p.N : (double*)p.D;
+    const int64_t ostr = p.ws ? 1 : 2, opart = p.ws ? 0 : part, old = p.ws ? p.N : p.ldd;
     int acc[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0;
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int col = n0 + (int)col0 + 8 * g + j;
-            if (col < p.N) Dd[2 * ((int64_t)row * p.ldd + col) + part] = ldexp(h8[j], er + p.eb[col] - 14);
+            if (col < p.N) Dd[ostr * ((int64_t)row * old + col) + opart] = ldexp(h8[j], er + p.eb[col] - 14);
           }
         }
       }
@@ -254,7 +263,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     if (nunits == 0 && row_ok) {
       for (int j = 0; j < 64; ++j) {
         const int col = n0 + (int)col0 + j;
-        if (col < p.N) Dd[2 * ((int64_t)row * p.ldd + col) + part] = 0.0;
+        if (col < p.N) Dd[ostr * ((int64_t)row * old + col) + opart] = 0.0;
       }
     }
   }
@@ -262,6 +271,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// D = sum over the K slices of their partials (real and imaginary planes), in slice order
+__global__ void oz_sum_slices_kernel(int M, int N, int nz, const double* ws, double2* D, int64_t ldd,
+                                     const int* active) {
+  if (active && *active == 0) return;
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int z = 0; z < nz; ++z) {
+      re += ws[(size_t)(2 * z) * total + e];
+      im += ws[(size_t)(2 * z + 1) * total + e];
+    }
+    D[(e / N) * ldd + (e % N)] = make_double2(re, im);
   }
 }
 
@@ -481,8 +505,10 @@ cudaError_t oz_split(OzOperand& op, void* mem, int rows, int K, const double2* X
   return cudaGetLastError();
 }
 
+size_t oz_split_k_doubles(int M, int N) { return (size_t)kOzSplitKMax * 2 * M * N; }
+
 cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, double2* D, int64_t ldd, int* err,
-                    cudaStream_t s, const int* active) {
+                    cudaStream_t s, const int* active, double* ws, size_t ws_doubles) {
   if (A.K != B.K || A.S != B.S || A.npl != 2 || B.npl != 3 || A.k_pad != B.k_pad) return cudaErrorInvalidValue;
   // the integer sums of one level hold at most S products of 2^24 per K chunk
   if (A.k_pad > 15 * OZ_KCHUNK) return cudaErrorInvalidValue;
@@ -508,13 +534,31 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
   p.ldd = ldd;
   p.err = err;
   p.active = active;
+  p.ws = nullptr;
+  p.kspan = p.k_pad;
+  int nz = 1;
+  if (ws) {
+    // grids that leave SMs idle (short M or N) cut K into slices until about one wave
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ctas = (B.rows_pad / OZ_TN) * 2 * p.mt;
+    const int kb = p.k_pad / OZ_TK;
+    int want = std::min(std::min(kOzSplitKMax, kb), sms / std::max(ctas, 1));
+    if (want >= 2) {
+      p.kspan = (kb + want - 1) / want * OZ_TK;
+      nz = (p.k_pad + p.kspan - 1) / p.kspan;
+      if ((size_t)nz * 2 * p.M * p.N <= ws_doubles) p.ws = ws;
+      else nz = 1, p.kspan = p.k_pad;
+    }
+  }
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(B.rows_pad / OZ_TN, 2 * p.mt);
+  dim3 grid(B.rows_pad / OZ_TN, 2 * p.mt, nz);
   void* kt0 = kt_enabled() ? kt_begin(s) : nullptr;
   oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(maps, p);
   LAUNCH_NOTE(1);
@@ -535,6 +579,12 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
       }
     const double pairs = (double)p.S * (p.S + 1) / 2;
     kt_end(kt0, 1, alg, alg * pairs, s);
+  }
+  if (p.ws) {
+    const int64_t total = (int64_t)p.M * p.N;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4 * 152);
+    oz_sum_slices_kernel<<<blocks, 256, 0, s>>>(p.M, p.N, nz, p.ws, D, ldd, active);
+    LAUNCH_NOTE(1);
   }
   return cudaGetLastError();
 }
