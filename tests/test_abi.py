@@ -72,3 +72,32 @@ def test_defaults_select_the_emulated_products():
     assert o.reduce_slices == 8 and o.refresh_window == 0 and o.deg_max == 48
     with pytest.raises(KeyError):
         gevp.default_opts(no_such_option=1)
+
+
+def _declared_param_counts():
+    """{name: number of parameters} for every function declared in include/*.h."""
+    counts = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(gevp_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+            params = m.group(2).strip()
+            counts[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return counts
+
+
+def test_binding_signatures_match_the_header():
+    # every ctypes argtypes list the binding sets has the header's parameter count
+    from paper_1007_4400_gb300 import gevp
+    L = gevp.load()
+    counts = _declared_param_counts()
+    checked = 0
+    for name, n in counts.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked >= 20
