@@ -77,11 +77,12 @@ typedef struct {
                         /* needed at least as many filter matvecs as the latest cold one, */
                         /* the next problem starts cold (the paper's refresh when progress */
                         /* flattens out, Sec. "A new computational philosophy")           */
-  int reduce_slices;    /* 0: the n^3 products of the reduction to standard form run on the */
-                        /* FP64 pipe. 1..8: they are emulated on the tensor cores with that */
-                        /* many 7-bit digits per entry (Ozaki scheme, exact digit products; */
-                        /* 8 digits keep FP64-class accuracy), see gevp_zgemm_emulated.    */
-                        /* gevp_solve_batched emulates its reduction one k-point at a time.  */
+  int reduce_slices;    /* 0: the products with an n x n operand (the reduction to standard */
+                        /* form, W = C Q, X = L^-H Q, A X, B X) run on the FP64 pipe. 1..8: */
+                        /* they are emulated on the tensor cores with that many 7-bit digits */
+                        /* per entry (Ozaki scheme, exact digit products; 8 digits keep     */
+                        /* FP64-class accuracy), see gevp_zgemm_emulated; the batched form  */
+                        /* emulates them one k-point at a time. Requires n <= 30720.        */
 } gevp_opts;
 
 /* Per-problem counters and CUDA-event phase times (milliseconds). */
