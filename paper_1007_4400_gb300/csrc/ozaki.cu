@@ -1,7 +1,8 @@
 // FP64 complex matrix products emulated on the tcgen05 tensor cores (Ozaki scheme):
 // D = op(A) op(B) with FP64-class accuracy from exact BF16 products. On this part an SM
 // retires two FP64 FMAs per clock but thousands of BF16 tensor flops, so the n^3 products
-// of the reduction to standard form run far faster this way than on the FP64 pipe.
+// of the reduction to standard form, and the n^2 m products with an n x n operand, run far
+// faster this way than on the FP64 pipe.
 //
 //  1. Splitting. Every row i of op(A) is scaled by 2^-e_i so that its largest real or
 //     imaginary part lies in [1/4, 1/2), rounded to the integer q = round(a 2^(7S))
@@ -27,9 +28,13 @@
 // the MMAs of one unit (digit pair, K chunk) into one of two TMEM accumulators (128
 // columns each) while warps 0-7 drain the other: each thread owns one row and 64 columns,
 // converts the exact FP32 sums to integers and adds them up per level; at the end of a
-// level the FP64 Horner state, kept in the upper 256 TMEM columns, is updated. All waits
-// are bounded; on expiry the kernel records an error code, stops issuing work, frees its
-// TMEM and returns.
+// level the FP64 Horner state, kept in the upper 256 TMEM columns, is updated. A grid that
+// would leave SMs idle (a short M or N) cuts K into slices whose FP64 partials a second
+// kernel sums in slice order; a device flag can make a launch a no-op (a converged batch
+// problem inside a captured graph). All waits are bounded; on expiry the kernel records an
+// error code, stops issuing work, waits (bounded) for the copies it issued, frees its TMEM
+// and returns. Operand rows come from the rows of a matrix or, through a transposing
+// splitter, from its columns.
 #include "gevp_internal.cuh"
 #include "tc_ptx.cuh"
 #include <cuda.h>
