@@ -44,3 +44,31 @@ def test_nominal_work_grows_with_size():
     w1 = b.nominal_flops_per_problem(2048, 140, 100, 20)
     w2 = b.nominal_flops_per_problem(4096, 140, 100, 20)
     assert w1 > 0 and w2 > 4 * w1   # the n^3 reduction dominates
+
+
+def _bench_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = _bench()
+    b.barrier(world)
+    t = b.max_over_ranks(1.5 + rank, world, "cpu")   # rank 1 is the slower one
+    b.barrier(world)
+    out.put((rank, t))
+    dist.destroy_process_group()
+
+
+def test_timing_is_the_max_over_two_gloo_ranks():
+    # the N > 1 bench reports the slowest rank's time on every rank
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 30500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_bench_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == {0: 2.5, 1: 2.5}
