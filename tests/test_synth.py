@@ -51,3 +51,29 @@ def test_lanczos_norm_estimate():
     P = synth.hermitian_part(torch.from_numpy(synth._cnormal(rng, (900, 900))))
     exact = float(torch.linalg.eigvalsh(P).abs().max())
     assert abs(synth._norm2_lanczos(P) - exact) <= 1e-3 * exact
+
+
+def test_deviation_angles_shrink_along_the_sequence(orc):
+    """The sequences behave as the paper reports for its SCF runs (Sec. "A new computational
+    philosophy", paragraph "Eigenvectors evolution"): the deviation angles of the matched
+    eigenvectors of consecutive problems are small and shrink as the sequence advances.
+    Oracle eigenvectors, the oracle's re-indexing."""
+    from oracle import pieces
+    from paper_1007_4400_gb300 import synth
+    n, nev = 120, 10
+    s = synth.make_sequence(1, n, 6, nev, 4)
+    B = s.B.numpy()
+    X = []
+    lam = []
+    for a in s.A:
+        lr, xr = orc.solve(a.numpy(), B, nev, method="jacobi")
+        lam.append(lr)
+        X.append(xr)
+    means = []
+    for l in range(len(X) - 1):
+        perm, _, nout = pieces.reindex(X[l], X[l + 1], B, lam[l], lam[l + 1])
+        c = pieces.overlap_cosines(X[l], X[l + 1], B)[np.arange(nev), perm]
+        theta = np.arccos(np.clip(c, 0.0, 1.0)) / (math.pi / 2)
+        means.append(theta.mean())
+    assert max(means) < 0.2
+    assert all(b < a for a, b in zip(means, means[1:]))
