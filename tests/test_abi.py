@@ -47,11 +47,25 @@ def test_host_only_calls_without_gpu():
 
 
 def test_binding_rejects_cpu_tensors():
+    # no CPU fallback: every tensor entry point refuses host tensors before any work
     import torch
     from paper_1007_4400_gb300 import gevp
     A = torch.eye(4, dtype=torch.complex128)
-    with pytest.raises(TypeError):
-        gevp.reduce(A, A)
+    Y = torch.zeros((4, 2), dtype=torch.complex128)
+    calls = [
+        lambda: gevp.reduce(A, A),
+        lambda: gevp.reduce(A, A, slices=8),
+        lambda: gevp.zgemm_emulated(A, A),
+        lambda: gevp.chebyshev_filter(A, Y, 2, 0.0, 1.0, -1.0),
+        lambda: gevp.cholqr2(Y),
+        lambda: gevp.rayleigh_ritz(A, Y),
+        lambda: gevp.heev_small(A),
+        lambda: gevp.matrix_variation(A, A),
+        lambda: gevp.deviation_angles(Y, Y),
+    ]
+    for call in calls:
+        with pytest.raises(TypeError):
+            call()
 
 
 def test_kernel_timing_records_nothing_without_launches():
