@@ -231,3 +231,31 @@ def test_oracle_pin_catches_planted_sign_error(orc):
     L, _ = orc.potrf(B)
     bad = orc.reduce(A.T.copy(), L)
     assert np.abs(L @ bad @ L.conj().T - A).max() > 1e-3
+
+
+def _read_golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    A, B, lam = [], [], None
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        tag, *vals = line.split()
+        if tag in ("A", "B"):
+            v = [float(x) for x in vals]
+            (A if tag == "A" else B).append([complex(v[2 * j], v[2 * j + 1]) for j in range(len(v) // 2)])
+        elif tag == "lambda":
+            lam = np.array([float(x) for x in vals])
+    return np.array(A), np.array(B), lam
+
+
+@pytest.mark.parametrize("name", ["pencil_2x2.txt", "pencil_3x3_block.txt"])
+def test_golden_pencils(orc, name):
+    """Hand-derived spectra stored in tests/golden (each file gives its derivation)."""
+    A, B, lam = _read_golden(name)
+    assert np.array_equal(A, A.conj().T) and np.array_equal(B, B.conj().T)
+    for method in ("jacobi", "tridiag"):
+        w, X = orc.solve(A, B, len(lam), method=method)
+        assert np.abs(w - lam).max() <= 1e-14 * np.abs(lam).max()
+        assert np.abs(A @ X - (B @ X) * w).max() <= 1e-13 * np.abs(lam).max()
