@@ -356,15 +356,16 @@ gevp_status gevp_probe_peaks(gevp_handle h, double* out);
 gevp_status gevp_chebyshev_filter_noalloc(void* stream, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy,
                                           int m, int degree, double lo, double hi, double s);
 
-/* Live timing of the two GEMM kernels, for measurement (off by default; process-wide).
+/* Live timing of the product kernels, for measurement (off by default; process-wide).
  * enable 1 clears earlier records and starts recording: every launch of the FP64 complex
- * GEMM and of the emulated product is bracketed by CUDA events on its own stream; 0 stops. */
+ * GEMM, of the emulated product and of the tall-skinny Gram kernel is bracketed by CUDA
+ * events on its own stream; 0 stops. */
 gevp_status gevp_kernel_timing(int enable);
-/* out (host, 8 doubles): for class 0 (FP64 complex GEMM) then class 1 (emulated product):
- * launches, total milliseconds, algorithmic flop (8 per complex multiply-add over the K
- * ranges the tiles process, at 64- resp. 128-row block granularity) and executed flop
- * (class 1: the digit pairs' BF16 real products, 36x the algorithmic at 8 digits). Waits
- * for the recorded events. */
+/* out (host, 12 doubles): for class 0 (FP64 complex GEMM), class 1 (emulated product) and
+ * class 2 (tall-skinny Gram kernel), four values each: launches, total milliseconds,
+ * algorithmic flop (8 per complex multiply-add over the K ranges the tiles process, at
+ * 64-, 128- resp. 16-row block granularity) and executed flop (class 1: the digit pairs'
+ * BF16 real products, 36x the algorithmic at 8 digits). Waits for the recorded events. */
 gevp_status gevp_kernel_timing_read(double* out);
 
 /* Number of kernels the handle launched since creation (for launch accounting). */

@@ -1,0 +1,317 @@
+// Tall-skinny kernels of the orthonormalisation (CholQR) and the Rayleigh-Ritz projection.
+//
+// zgram: G = X^H Y for n x mx and n x my blocks with n >> m (the Gram matrix Y^H Y of
+//   CholQR, the projection Q^H W of Rayleigh-Ritz, the overlaps Q_lock^H Y). On this part
+//   one SM retires about 1.7 FP64 FMAs per clock, so the product is FP64-pipe bound and
+//   the whole job is to keep all 152 SMs busy with little else: the m x m result is cut
+//   into 16 x 16 tiles (only the lower ones when the result is Hermitian, half the
+//   flops), n into slices so that the CTAs cover the SMs several times over, and the
+//   slices of a tile are summed in slice order by whichever CTA of that tile finishes
+//   last (a per-tile arrival counter), so there is no second launch and the sum is
+//   deterministic. A Hermitian result is written to both triangles.
+//
+// cholinv: the Cholesky factor L of D W D + shift I (W the Gram matrix, lower triangle
+//   read; D = diag(W)^-1/2 the column scaling of CholQR) and its inverse, for m up to a
+//   few hundred, in the CTAs of one thread-block cluster. A one-CTA factorisation would
+//   take close to a millisecond at m = 140 (m^3/3 complex multiply-adds at two FP64 FMAs
+//   per clock); the blocked right-looking form over all SMs spends most of its time in
+//   launches and serial diagonal blocks. Here the rows are dealt cyclically to the P CTAs
+//   (row i to CTA i mod P) and held in shared memory with the rows of the inverse; column
+//   j of the factor and row j of the inverse are exchanged through distributed shared
+//   memory, one cluster barrier per column:
+//     step j: every CTA reads the pivot a_jj, the column A[j+1:m, j] and the row S[j, 0:j]
+//     (values final after step j-1), then updates its own rows i > j:
+//       A[i, e] -= A[i, j] conj(A[e, j]) / a_jj   (j < e <= i; the trailing Cholesky update)
+//       S[i, e] -= A[i, j] S[j, e] / a_jj         (e <= j; the inverse, L X = I, right-looking)
+//     L[i, j] = A[i, j] / sqrt(a_jj) and (L^-1)[i, e] = S[i, e] / sqrt(a_ii) are read off at
+//     the end. Within a step the reads (column j, row j, the pivot) and the writes
+//     (columns > j of A, rows > j of S) never meet, so one barrier per step suffices.
+//   The output Li = L^-1 D (columns scaled by D) makes Y Li^H = Y D L^-H, the orthonormal
+//   factor of one CholQR pass, a single product. A non-positive pivot stops the cluster
+//   (every CTA reads the same pivot, so the decision is uniform) and sets *info to its
+//   1-based index.
+#include "gevp_internal.cuh"
+#include <cooperative_groups.h>
+#include <algorithm>
+
+namespace gevp {
+
+namespace {
+
+constexpr int GT = 16;   // zgram output tile edge
+constexpr int GK = 16;   // rows staged per step
+
+__global__ void __launch_bounds__(256) zgram_kernel(int64_t n, int mx, int my, const double2* __restrict__ X,
+                                                    int64_t ldx, const double2* __restrict__ Y, int64_t ldy,
+                                                    double2* G, int64_t ldg, int herm, int ntj, int slices,
+                                                    int64_t per, double2* part, unsigned* cnt) {
+  __shared__ double2 Xs[GK][GT];
+  __shared__ double2 Ys[GK][GT];
+  __shared__ int last;
+  const int tile = blockIdx.x;
+  const int ti = tile / ntj, tj = tile % ntj;
+  if (herm && tj > ti) return;
+  const int slice = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int ty = tid / GT, tx = tid % GT;
+  const int64_t k0 = (int64_t)slice * per;
+  const int64_t k1 = min(n, k0 + per);
+  const int lr = tid / GT, lc = tid % GT;   // staging: row lr, column lc of the tile
+  const int xc = ti * GT + lc, yc = tj * GT + lc;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t k = k0; k < k1; k += GK) {
+    const int64_t kr = k + lr;
+    Xs[lr][lc] = (kr < k1 && xc < mx) ? X[kr * ldx + xc] : make_double2(0.0, 0.0);
+    Ys[lr][lc] = (kr < k1 && yc < my) ? Y[kr * ldy + yc] : make_double2(0.0, 0.0);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) zfma(acc, zconj(Xs[kk][ty]), Ys[kk][tx]);
+    __syncthreads();
+  }
+  const int i = ti * GT + ty, j = tj * GT + tx;
+  if (slices > 1) {
+    part[((int64_t)tile * slices + slice) * (GT * GT) + tid] = acc;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(&cnt[tile], 1u) == (unsigned)(slices - 1));
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    acc = make_double2(0.0, 0.0);
+    const double2* p = part + (int64_t)tile * slices * (GT * GT) + tid;
+    for (int s = 0; s < slices; ++s) acc = zadd(acc, __ldcg(p + (int64_t)s * (GT * GT)));
+    if (tid == 0) cnt[tile] = 0u;   // ready for the next launch (stream order)
+  }
+  if (i >= mx || j >= my) return;
+  if (!herm) {
+    G[(int64_t)i * ldg + j] = acc;
+    return;
+  }
+  if (j > i) return;   // the diagonal tile's upper half comes from the lower one
+  if (j == i) {
+    G[(int64_t)i * ldg + i] = make_double2(acc.x, 0.0);
+  } else {
+    G[(int64_t)i * ldg + j] = acc;
+    G[(int64_t)j * ldg + i] = zconj(acc);
+  }
+}
+
+constexpr int CT = 256;          // threads per cholinv CTA
+constexpr int kCholInvMax = 320; // largest order (shared-memory bound at 16 CTAs)
+
+template <int P>
+__global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const double2* __restrict__ W, int64_t ldw,
+                                                                double shift, double2* Li, int64_t ldi,
+                                                                double2* Lf, int64_t ldl, int* info) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double2 csm[];
+  __shared__ double2 cbuf[kCholInvMax];   // column j of A (raw), rows > j
+  __shared__ double2 xbuf[kCholInvMax];   // row j of S (raw), columns <= j
+  __shared__ double2 cs[kCholInvMax / 8]; // own rows' A[i, j] / a_jj
+  __shared__ double dsc[kCholInvMax];     // D
+  __shared__ double piv[kCholInvMax];     // sqrt(a_jj)
+  __shared__ double2* rA[P];
+  __shared__ double2* rS[P];
+  __shared__ double apiv, inv2;
+  const int tid = threadIdx.x;
+  const int rank = (int)cl.block_rank();
+  const int R = (m + P - 1) / P;
+  double2* Arow = csm;            // [R][m]: own rows i = rank + P t of the matrix being factored
+  double2* Srow = csm + R * m;    // [R][m]: own rows of the inverse's accumulator
+  if (tid < P) {
+    rA[tid] = cl.map_shared_rank(Arow, tid);
+    rS[tid] = cl.map_shared_rank(Srow, tid);
+  }
+  for (int i = tid; i < m; i += CT) {
+    const double v = W[(int64_t)i * ldw + i].x;
+    dsc[i] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < R * m; e += CT) {
+    const int t = e / m, c = e % m, i = rank + P * t;
+    double2 a = make_double2(0.0, 0.0), s = make_double2(0.0, 0.0);
+    if (i < m && c <= i) {
+      a = zscale(W[(int64_t)i * ldw + c], dsc[i] * dsc[c]);
+      if (c == i) a = make_double2(a.x + shift, 0.0);
+      if (c == i) s = make_double2(1.0, 0.0);
+    }
+    Arow[e] = a;
+    Srow[e] = s;
+  }
+  cl.sync();
+  bool failed = false;
+  for (int j = 0; j < m; ++j) {
+    const int oj = j % P, tjj = j / P;
+    for (int l = tid; l < m; l += CT) {
+      if (l > j) {
+        cbuf[l] = rA[l % P][(l / P) * m + j];
+      } else {
+        xbuf[l] = rS[oj][tjj * m + l];
+        if (l == j) apiv = rA[oj][tjj * m + j].x;
+      }
+    }
+    __syncthreads();
+    const double a = apiv;   // the same value in every CTA: a uniform decision
+    if (!(a > 0.0)) {
+      if (rank == 0 && tid == 0) atomicCAS(info, 0, j + 1);
+      failed = true;
+      break;
+    }
+    if (tid == 0) {
+      const double ri = rsqrt(a);
+      piv[j] = a * ri;
+      inv2 = ri * ri;
+    }
+    __syncthreads();
+    // own rows below the pivot: i = rank + P t > j
+    const int t0 = j >= rank ? (j - rank) / P + 1 : 0;
+    int t1 = R;
+    while (t1 > t0 && rank + P * (t1 - 1) >= m) --t1;
+    const int nr = t1 - t0;
+    if (tid < nr) cs[tid] = zscale(cbuf[rank + P * (t0 + tid)], inv2);
+    __syncthreads();
+    for (int idx = tid; idx < nr * m; idx += CT) {
+      const int tt = idx / m, e = idx % m, t = t0 + tt, i = rank + P * t;
+      if (e > i) continue;
+      const double2 li = cs[tt];
+      if (e <= j) {
+        double2 v = Srow[t * m + e];
+        zfma(v, zscale(li, -1.0), xbuf[e]);
+        Srow[t * m + e] = v;
+      } else {
+        double2 v = Arow[t * m + e];
+        zfma(v, zscale(li, -1.0), zconj(cbuf[e]));
+        Arow[t * m + e] = v;
+      }
+    }
+    cl.sync();
+  }
+  if (failed) {
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+    return;
+  }
+  // read off L and L^-1 D for the own rows
+  for (int e = tid; e < R * m; e += CT) {
+    const int t = e / m, c = e % m, i = rank + P * t;
+    if (i >= m) continue;
+    double2 x = make_double2(0.0, 0.0);
+    if (c <= i) x = zscale(Srow[e], dsc[c] / piv[i]);
+    Li[(int64_t)i * ldi + c] = x;
+    if (Lf) {
+      double2 l = make_double2(0.0, 0.0);
+      if (c < i) l = zscale(Arow[e], 1.0 / piv[c]);
+      else if (c == i) l = make_double2(piv[i], 0.0);
+      Lf[(int64_t)i * ldl + c] = l;
+    }
+  }
+}
+
+template <int P>
+size_t cholinv_smem(int m) {
+  return (size_t)2 * ((m + P - 1) / P) * m * sizeof(double2);
+}
+
+template <int P>
+bool cholinv_launch(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
+                    int64_t ldl, int* info, cudaStream_t s) {
+  const size_t smem = cholinv_smem<P>(m);
+  if (smem > 200 * 1024) return false;
+  static int ready = 0;   // 0 unknown, 1 usable, -1 not launchable on this device
+  if (ready < 0) return false;
+  if (ready == 0) {
+    ready = -1;
+    if (P > 8 && cudaFuncSetAttribute(cholinv_cluster_kernel<P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                     cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaFuncSetAttribute(cholinv_cluster_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t probe = {};
+    probe.gridDim = dim3(P, 1, 1);
+    probe.blockDim = dim3(CT, 1, 1);
+    probe.dynamicSmemBytes = 200 * 1024;
+    cudaLaunchAttribute pa[1];
+    pa[0].id = cudaLaunchAttributeClusterDimension;
+    pa[0].val.clusterDim.x = P;
+    pa[0].val.clusterDim.y = 1;
+    pa[0].val.clusterDim.z = 1;
+    probe.attrs = pa;
+    probe.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, cholinv_cluster_kernel<P>, &probe) != cudaSuccess ||
+        nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    ready = 1;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P, 1, 1);
+  cfg.blockDim = dim3(CT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = P;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, cholinv_cluster_kernel<P>, m, W, ldw, shift, Li, ldi, Lf, ldl, info) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  LAUNCH_NOTE(1);
+  return true;
+}
+
+constexpr int kSMs = 152;
+
+}  // namespace
+
+int cholinv_max_order() { return kCholInvMax; }
+
+bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
+                   int64_t ldl, int* info, cudaStream_t s) {
+  if (m < 1 || m > kCholInvMax) return false;
+  if (cholinv_launch<16>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, s)) return true;
+  return cholinv_launch<8>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, s);
+}
+
+size_t zgram_counters() { return 4096; }
+
+void zgram(int64_t n, int mx, int my, const double2* X, int64_t ldx, const double2* Y, int64_t ldy, double2* G,
+           int64_t ldg, int herm, double2* part, size_t part_elems, unsigned* cnt, cudaStream_t s) {
+  if (mx <= 0 || my <= 0) return;
+  const int nti = (mx + GT - 1) / GT, ntj = (my + GT - 1) / GT;
+  const int64_t tiles = (int64_t)nti * ntj;
+  const int64_t active = herm ? (int64_t)nti * (nti + 1) / 2 : tiles;
+  // slices: about eight CTAs per SM over the active tiles (the FP64 pipe is the limit, so
+  // the point is an even spread), at least 2 GK rows each, within the partials' room and
+  // the counters
+  int64_t slices = (8 * kSMs + active - 1) / active;
+  slices = std::min<int64_t>(slices, std::max<int64_t>(1, n / (2 * GK)));
+  if (tiles > (int64_t)zgram_counters() || !part) slices = 1;
+  while (slices > 1 && (size_t)(tiles * slices * GT * GT) > part_elems) slices /= 2;
+  if (n == 0) slices = 1;
+  int64_t per = (n + slices - 1) / slices;
+  per = (per + GK - 1) / GK * GK;
+  slices = n > 0 ? (n + per - 1) / per : 1;
+  dim3 grid((unsigned)tiles, (unsigned)slices);
+  void* kt0 = kt_enabled() ? kt_begin(s) : nullptr;
+  zgram_kernel<<<grid, GT * GT, 0, s>>>(n, mx, my, X, ldx, Y, ldy, G, ldg, herm, ntj, (int)slices, per, part, cnt);
+  LAUNCH_NOTE(1);
+  if (kt0) {
+    // work: 8 flop per complex multiply-add of the tiles formed (16 x 16 granularity)
+    const double f = 8.0 * (double)active * (GT * GT) * (double)n;
+    kt_end(kt0, 2, f, f, s);
+  }
+}
+
+}  // namespace gevp

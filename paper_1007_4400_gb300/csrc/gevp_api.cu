@@ -54,6 +54,7 @@ struct gevp_ctx {
   double *theta = nullptr, *res = nullptr, *dscale = nullptr, *partial = nullptr, *bounds = nullptr,
          *lam = nullptr, *resf = nullptr;
   int *info = nullptr, *flag = nullptr;
+  unsigned* gcnt = nullptr;                 // arrival counters of the Gram kernel's split finish
   unsigned long long* vscratch = nullptr;   // matrix-variation reductions and thresholds
   unsigned long long* vd2 = nullptr;        // matrix-variation squared moduli (grown on demand)
   size_t vd2_bytes = 0;
@@ -208,6 +209,8 @@ size_t layout(gevp_ctx* h, char* base, int64_t n, int m) {
   h->bounds = (double*)take(16 * 8);
   h->info = (int*)take(64);
   h->flag = (int*)take(64);
+  h->gcnt = (unsigned*)take(zgram_counters() * sizeof(unsigned));
+  h->hw.gcnt = h->gcnt;
   h->vscratch = (unsigned long long*)take(64 * 8);
   return off;
 }
@@ -234,6 +237,7 @@ gevp_status ensure(gevp_ctx* h, int64_t n, int m) {
   h->arena = (char*)p;
   h->arena_bytes = bytes;
   layout(h, h->arena, nn, mm);
+  CK(cudaMemsetAsync(h->gcnt, 0, zgram_counters() * sizeof(unsigned), h->stream));
   h->cap_n = nn;
   h->cap_m = mm;
   h->chol_valid = false;
@@ -493,21 +497,49 @@ gevp_status ensure_pipeline(gevp_ctx* h) {
   return GEVP_OK;
 }
 
+// One CholQR pass on the tall-skinny kernels: W = src^H src (lower tiles, one launch),
+// Li = L^-1 D with D W D + sh I = L L^H (one cluster launch, *info set on a non-positive
+// pivot), dst = src Li^H = src D L^-H. False if the cluster factorisation is not available
+// for this order (nothing enqueued after the Gram matrix then).
+bool cholqr_pass(gevp_ctx* h, int64_t n, int ma, const double2* src, int64_t lds, double2* dst, int64_t ldd, double sh,
+                 int* info) {
+  if (ma > cholinv_max_order()) return false;
+  zgram(n, ma, ma, src, lds, src, lds, h->Gw, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
+  if (!cholinv_small(ma, h->Gw, ma, sh, h->Gwi, ma, nullptr, 0, info, h->stream)) return false;
+  ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
+  q.triB = 2;
+  zgemm(q, h->split, h->split_elems, h->stream);
+  return true;
+}
+
 // Orthonormalise Y (n x ma, ld ldy) against Q[:, 0:nlock] and by CholQR2; result in Out.
-// A pass whose Gram matrix is not numerically positive definite is repeated as shifted
-// CholQR (Fukaya et al. 2020); the result is accepted only after two consecutive plain
-// passes (so a shifted pass is always followed by CholQR2). A block that stays rank
-// deficient is replaced by fresh random columns (projected against the locked ones).
+// The usual case, two plain passes that both succeed, is enqueued at once (the first into
+// the free block Xf, the second into Out, so Y is still intact if a pass fails) with a
+// single status read after both. Otherwise a pass whose Gram matrix is not numerically
+// positive definite is repeated as shifted CholQR (Fukaya et al. 2020); the result is
+// accepted only after two consecutive plain passes (so a shifted pass is always followed
+// by CholQR2). A block that stays rank deficient is replaced by fresh random columns
+// (projected against the locked ones).
 gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_t ldy, int ma, double2* Out,
                            int64_t ldo, gevp_stats* st, uint64_t seed = 0) {
   const int64_t ldq = h->cap_m;
+  const bool fast = ma <= cholinv_max_order();
   for (int restart = 0; restart < 2; ++restart) {
     for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
-      ZgemmArgs p = zg(nlock, ma, (int)n, h->Q, ldq, 1, Y, ldy, 0, h->P, ma);
-      zgemm(p, h->split, h->split_elems, h->stream);
+      zgram(n, nlock, ma, h->Q, ldq, Y, ldy, h->P, ma, 0, h->split, h->split_elems, h->gcnt, h->stream);
       ZgemmArgs u = zg((int)n, ma, nlock, h->Q, ldq, 0, h->P, ma, 0, Y, ldy, -1.0);
       u.Cin = Y; u.ldc = ldy; u.beta = 1.0;
       zgemm(u, h->split, h->split_elems, h->stream);
+    }
+    if (fast && restart == 0) {
+      CK(cudaMemsetAsync(h->info, 0, 2 * sizeof(int), h->stream));
+      if (cholqr_pass(h, n, ma, Y, ldy, h->Xf, ldq, 0.0, h->info) &&
+          cholqr_pass(h, n, ma, h->Xf, ldq, Out, ldo, 0.0, h->info + 1)) {
+        int inf[2] = {0, 0};
+        TRY(sync_read(h, h->info, inf, sizeof inf));
+        if (st) st->flops_fp64 += 2 * 8.0 * (double)n * ma * ma;
+        if (inf[0] == 0 && inf[1] == 0) return GEVP_OK;
+      }
     }
     double2* src = Y;
     int64_t lds = ldy;
@@ -517,21 +549,30 @@ gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_
     bool failed = false;
     for (int pass = 0; pass < 6 && plain_ok < 2; ++pass) {
       bool shifted = false;
+      bool clustered = false;
       int attempt = 0;
       for (; attempt < 3; ++attempt) {
-        ZgemmArgs g = zg(ma, ma, (int)n, src, lds, 1, src, lds, 0, h->Gw, ma);
-        g.triD = 1;
-        zgemm(g, h->split, h->split_elems, h->stream);
-        hermitize_lower(ma, h->Gw, ma, h->stream);
-        gram_scale(ma, h->Gw, ma, h->dscale, h->stream);
+        double sh = 0.0;
         if (shifted) {
           // s = 11 (n m + m (m+1)) u ||Y D||_2^2 with ||Y D||_F^2 = m, grown 100x per retry
           double u = 1.1102230246251565e-16;
-          double sh = 11.0 * ((double)n * ma + (double)ma * (ma + 1)) * u * ma * std::pow(100.0, attempt - 1);
-          zshift_diag(ma, h->Gw, ma, sh, h->stream);
+          sh = 11.0 * ((double)n * ma + (double)ma * (ma + 1)) * u * ma * std::pow(100.0, attempt - 1);
         }
         CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
-        potrf_lower(ma, h->Gw, ma, h->info, h->Gwi, ma, h->stream);
+        clustered = false;
+        if (fast) {
+          zgram(n, ma, ma, src, lds, src, lds, h->Gw, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
+          clustered = cholinv_small(ma, h->Gw, ma, sh, h->Gwi, ma, nullptr, 0, h->info, h->stream);
+        }
+        if (!clustered) {
+          ZgemmArgs g = zg(ma, ma, (int)n, src, lds, 1, src, lds, 0, h->Gw, ma);
+          g.triD = 1;
+          zgemm(g, h->split, h->split_elems, h->stream);
+          hermitize_lower(ma, h->Gw, ma, h->stream);
+          gram_scale(ma, h->Gw, ma, h->dscale, h->stream);
+          if (shifted) zshift_diag(ma, h->Gw, ma, sh, h->stream);
+          potrf_lower(ma, h->Gw, ma, h->info, h->Gwi, ma, h->stream);
+        }
         int info = 0;
         TRY(sync_read(h, h->info, &info, sizeof(int)));
         if (info == 0) break;
@@ -540,12 +581,14 @@ gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_
       }
       if (attempt == 3) { failed = true; break; }
       plain_ok = shifted ? 0 : plain_ok + 1;
-      trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream, true);
-      zcol_scale(n, ma, src, lds, h->dscale, h->stream);
+      if (!clustered) {
+        trtri_lower(ma, h->Gw, ma, h->Gwi, ma, h->trtri_ws, h->trtri_elems, h->stream, true);
+        zcol_scale(n, ma, src, lds, h->dscale, h->stream);
+      }
       ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
       q.triB = 2;
       zgemm(q, h->split, h->split_elems, h->stream);
-      if (st) st->flops_fp64 += 8.0 * (double)n * ma * ma * 1.5;
+      if (st) st->flops_fp64 += 8.0 * (double)n * ma * ma;
       std::swap(src, dst);
       std::swap(lds, ldd);
     }
@@ -572,14 +615,16 @@ gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const doubl
     ZgemmArgs w = zg((int)n, ma, (int)n, C, ldc, 0, Qa, ld, 0, h->Wt, ld);
     zgemm(w, h->split, h->split_elems, h->stream);
   }
-  ZgemmArgs g = zg(ma, ma, (int)n, Qa, ld, 1, h->Wt, ld, 0, h->G, ma);
-  zgemm(g, h->split, h->split_elems, h->stream);
+  // G = Q^H C Q is Hermitian: its lower tiles only, both triangles written
+  zgram(n, ma, ma, Qa, ld, h->Wt, ld, h->G, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
   heev_small(ma, h->G, ma, h->theta + nlock, h->Zs, ma, h->hw, refine, h->stream);
+  // [Q W] <- [Q Wt] Z in one launch (a batch of two products sharing Z; Q's goes through Y1)
   ZgemmArgs q = zg((int)n, ma, ma, Qa, ld, 0, h->Zs, ma, 0, h->Y1, ld);
+  q.batch = 2;
+  q.sA = h->Wt - Qa;
+  q.sD = (h->W + nlock) - h->Y1;
   zgemm(q, h->split, h->split_elems, h->stream);
   zcopy2d(n, ma, h->Y1, ld, Qa, ld, h->stream);
-  ZgemmArgs ww = zg((int)n, ma, ma, h->Wt, ld, 0, h->Zs, ma, 0, h->W + nlock, ld);
-  zgemm(ww, h->split, h->split_elems, h->stream);
   resid_norms(n, ma, h->W + nlock, ld, Qa, ld, h->theta + nlock, h->res + nlock, h->partial, h->stream);
   if (st) st->flops_fp64 += 8.0 * ((double)n * n * ma + 3.0 * n * ma * ma) + 32.0 * refine * (double)ma * ma * ma;
   return GEVP_OK;

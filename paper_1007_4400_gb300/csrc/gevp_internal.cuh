@@ -117,6 +117,7 @@ struct HeevWork {
   double* lam;                  // m
   double2* split_ws; size_t split_ws_elems;
   double* scal;                 // small scalars
+  unsigned* gcnt;               // zgram arrival counters (zgram_counters() words, zero)
 };
 size_t heev_ws_bytes(int m, size_t split_elems);
 void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Z, int64_t ldz,
@@ -145,6 +146,20 @@ void final_check(int64_t n, int m, const double2* X, const double2* AX, const do
                  double* lam_io, double* res_out, double normA, double* partial, cudaStream_t s);
 // Cholesky-QR helpers
 void gram_scale(int m, double2* W, int64_t ldw, double* dscale, cudaStream_t s); // W <- D W D, D = diag(W)^-1/2
+// G = X^H Y (X n x mx, Y n x my; G mx x my, ld ldg) on the FP64 pipe, split over n with a
+// fixed-order finish in the same launch; herm = 1: the result is Hermitian (mx = my), only
+// its lower tiles are formed and both triangles written. part: partials scratch (may be
+// null: no split), cnt: zgram_counters() words, zero on first use (left zero).
+size_t zgram_counters();
+void zgram(int64_t n, int mx, int my, const double2* X, int64_t ldx, const double2* Y, int64_t ldy, double2* G,
+           int64_t ldg, int herm, double2* part, size_t part_elems, unsigned* cnt, cudaStream_t s);
+// Li = L^-1 D (lower, ld ldi) and optionally Lf = L, where D W D + shift I = L L^H, W m x m
+// (lower triangle read), D = diag(W)^-1/2 (1 where a diagonal entry is not positive), in
+// one thread-block cluster. *info <- 1-based index of a non-positive pivot (atomicCAS from
+// 0). false: not launchable (m > cholinv_max_order() or no cluster): nothing was enqueued.
+int cholinv_max_order();
+bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
+                   int64_t ldl, int* info, cudaStream_t s);
 
 // ---------------------------------------------------------------- backward
 // GA = gE X X^H, GB = -gE X diag(lam) X^H (lower tiles by GEMM, then Hermitian completion).
@@ -317,7 +332,8 @@ extern int64_t g_launches;
 #define LAUNCH_NOTE(k) (::gevp::g_launches += (k))
 
 // ---------------------------------------------------------------- live kernel timing
-// Classes: 0 the FP64 complex GEMM (zgemm_kernel), 1 the emulated product (oz_gemm_kernel).
+// Classes: 0 the FP64 complex GEMM (zgemm_kernel), 1 the emulated product (oz_gemm_kernel),
+// 2 the tall-skinny Gram kernel (zgram_kernel).
 // kt_begin records an event on s and returns it (only call when kt_enabled()); kt_end
 // records the closing event with the launch's algorithmic and executed flop.
 bool kt_enabled();

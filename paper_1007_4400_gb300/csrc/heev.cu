@@ -479,11 +479,17 @@ __device__ double block_sum_d(double v, double* red) {
 }
 
 // Ogita-Aishima: lam_i = Re S_ii / (1 - Re R_ii); delta = 2 (||S - diag(lam)||_F + ||G||_F ||R||_F).
-// scal[0] = delta, scal[1] = ||G||_F (input, computed once).
+// scal[0] = delta, scal[1] = ||G||_F (input, computed once). The kernels are given the Gram
+// matrix Zg = Z^H Z and use R = I - Zg.
 // The same scalars over many CTAs (one SM retires about two FP64 FMAs per clock, so the
 // m^2 sums of one CTA take tens of microseconds): per-block partial sums, then one thread
 // adds them in block order (deterministic). lam is written by the diagonal's owners.
-__global__ void __launch_bounds__(256) oa_partial_kernel(int m, const double2* R, const double2* S, double* lam,
+__device__ __forceinline__ double2 oa_r(const double2* Zg, int64_t e, int i, int j) {
+  const double2 g = Zg[e];
+  return make_double2((i == j ? 1.0 : 0.0) - g.x, -g.y);
+}
+
+__global__ void __launch_bounds__(256) oa_partial_kernel(int m, const double2* Zg, const double2* S, double* lam,
                                                          double* part) {
   __shared__ double red[32];
   double soff = 0.0, r2 = 0.0;
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(256) oa_partial_kernel(int m, const double2* R
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mm; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / m), j = (int)(e % m);
     double2 sv = S[e];
-    const double2 rv = R[e];
+    const double2 rv = oa_r(Zg, e, i, j);
     if (i == j) {
       const double li = sv.x / (1.0 - rv.x);
       lam[i] = li;
@@ -536,13 +542,13 @@ __global__ void frob_finish_kernel(int nblk, const double* part, double* out) {
   out[0] = sqrt(s);
 }
 
-__global__ void oa_update_kernel(int m, const double2* R, const double2* S, const double* lam, const double* scal,
+__global__ void oa_update_kernel(int m, const double2* Zg, const double2* S, const double* lam, const double* scal,
                                  double2* E, int only_orth) {
   int64_t total = (int64_t)m * m;
   double delta = only_orth ? 1e300 : scal[0];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / m), j = (int)(e % m);
-    double2 r = R[e];
+    double2 r = oa_r(Zg, e, i, j);
     double2 v;
     double d = lam[j] - lam[i];
     v = zscale(r, 0.5);
@@ -557,6 +563,34 @@ __global__ void oa_update_kernel(int m, const double2* R, const double2* S, cons
   }
 }
 
+
+// Zn = Z + Z E with the product Z E in FP32 (FP32 FMA runs 64x faster than FP64 here). E
+// is the refinement's correction: its entries are at most 0.2 and shrink quadratically, so
+// the FP32 product's error (about 1e-7 |E|) is far below the quadratic error the next step
+// removes anyway; every step recomputes Z^H Z and Z^H G Z in FP64 from the new Z, and the
+// sum with Z is in FP64, so the iteration still converges to FP64 accuracy.
+__global__ void __launch_bounds__(256) zupd32_kernel(int m, const double2* Z, const double2* E, double2* Zn) {
+  __shared__ float2 Zs[16][17];
+  __shared__ float2 Es[16][17];
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < m; k0 += 16) {
+    const int kz = k0 + tx, ke = k0 + ty;
+    double2 z = (i < m && kz < m) ? Z[(int64_t)i * m + kz] : make_double2(0.0, 0.0);
+    double2 e = (ke < m && j < m) ? E[(int64_t)ke * m + j] : make_double2(0.0, 0.0);
+    Zs[ty][tx] = make_float2((float)z.x, (float)z.y);
+    Es[ty][tx] = make_float2((float)e.x, (float)e.y);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) cfma(acc, Zs[ty][kk], Es[kk][tx]);
+    __syncthreads();
+  }
+  if (i < m && j < m) {
+    const double2 z = Z[(int64_t)i * m + j];
+    Zn[(int64_t)i * m + j] = make_double2(z.x + (double)acc.x, z.y + (double)acc.y);
+  }
+}
 
 // Clusters the refinement leaves mixed (pairs closer than its threshold): S = Z^H G Z is
 // diagonal apart from those couplings. One CTA finds the pairs with |s_pq| above tol and
@@ -787,17 +821,14 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   LAUNCH_NOTE(2);
   double2* Z = w.Z;
   double2* Zn = w.T;   // ping-pong partner
+  const dim3 ugrid((m + 15) / 16, (m + 15) / 16);
   for (int it = 0; it <= refine_iters; ++it) {
-    // R = I - Z^H Z
-    zset_identity(m, m, w.R, m, s);
-    ZgemmArgs a = zg(m, m, m, Z, m, 1, Z, m, 0, w.R, m, -1.0);
-    a.Cin = w.R; a.ldc = m; a.beta = 1.0;
-    zgemm(a, w.split_ws, w.split_ws_elems, s);
-    // E <- G Z (E used as scratch), S = Z^H (G Z)
+    // R = I - Z^H Z (the kernels below are given Z^H Z; Hermitian: lower tiles only)
+    zgram(m, m, m, Z, m, Z, m, w.R, m, 1, w.split_ws, w.split_ws_elems, w.gcnt, s);
+    // E <- G Z (E used as scratch), S = Z^H (G Z) (Hermitian: lower tiles only)
     ZgemmArgs b = zg(m, m, m, G, ldg, 0, Z, m, 0, w.E, m);
     zgemm(b, w.split_ws, w.split_ws_elems, s);
-    ZgemmArgs c = zg(m, m, m, Z, m, 1, w.E, m, 0, w.S, m);
-    zgemm(c, w.split_ws, w.split_ws_elems, s);
+    zgram(m, m, m, Z, m, w.E, m, w.S, m, 1, w.split_ws, w.split_ws_elems, w.gcnt, s);
     // partial sums in E: the product G Z it held has been consumed by S = Z^H (G Z)
     oa_partial_kernel<<<nblk, 256, 0, s>>>(m, w.R, w.S, w.lam, part);
     oa_finish_kernel<<<1, 32, 0, s>>>(nblk, part, w.scal);
@@ -806,19 +837,16 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
     // Newton-Schulz step) and yields Rayleigh quotients of the vectors it returns
     oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, it == refine_iters ? 1 : 0);
     LAUNCH_NOTE(1);
-    // Zn = Z + Z E
-    ZgemmArgs d = zg(m, m, m, Z, m, 0, w.E, m, 0, Zn, m);
-    d.Cin = Z; d.ldc = m; d.beta = 1.0;
-    zgemm(d, w.split_ws, w.split_ws_elems, s);
+    // Zn = Z + Z E (the correction's product in FP32)
+    zupd32_kernel<<<ugrid, 256, 0, s>>>(m, Z, w.E, Zn);
+    LAUNCH_NOTE(1);
     std::swap(Z, Zn);
   }
   // resolve what the refinement left mixed: S = Z^H G Z, exact rotations on its remaining
   // couplings (near-degenerate clusters), eigenvalues = diag(S)
   ZgemmArgs b2 = zg(m, m, m, G, ldg, 0, Z, m, 0, w.E, m);
   zgemm(b2, w.split_ws, w.split_ws_elems, s);
-  ZgemmArgs c2 = zg(m, m, m, Z, m, 1, w.E, m, 0, w.S, m);
-  zgemm(c2, w.split_ws, w.split_ws_elems, s);
-  hermitize_avg(m, w.S, m, s);
+  zgram(m, m, m, Z, m, w.E, m, w.S, m, 1, w.split_ws, w.split_ws_elems, w.gcnt, s);
   cluster_jacobi_kernel<<<1, 1024, 0, s>>>(m, w.S, Z, w.lam, w.scal + 1, 1e-15, 12);
   LAUNCH_NOTE(1);
   sort_pairs_kernel<<<1, 1024, 0, s>>>(m, w.lam, Z, theta, Zout, ldz);

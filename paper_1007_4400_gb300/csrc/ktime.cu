@@ -1,7 +1,7 @@
-// Live timing of the GEMM kernels, for measurement: while enabled, every launch of the FP64
-// complex GEMM and of the emulated product is bracketed by a CUDA event pair recorded on
-// its own stream, together with the launch's work (flop at 64-block granularity of its K
-// ranges). Reading waits for the events and sums per kernel class. Off by default; the
+// Live timing of the product kernels, for measurement: while enabled, every launch of the
+// FP64 complex GEMM, of the emulated product and of the tall-skinny Gram kernel is bracketed
+// by a CUDA event pair recorded on its own stream, together with the launch's work (flop
+// over the K ranges its tiles process). Reading waits for the events and sums per kernel class. Off by default; the
 // cost when off is one branch per launch.
 #include "gevp_internal.cuh"
 #include "../../include/gevp.h"
@@ -10,6 +10,8 @@
 #include <vector>
 
 namespace gevp {
+
+constexpr int kKtClasses = 3;
 
 namespace {
 
@@ -107,7 +109,7 @@ gevp_status gevp_kernel_timing_read(double* out) {
   if (!out) return GEVP_ERR_INVALID_ARG;
   gevp::KtState& k = gevp::kt();
   std::lock_guard<std::mutex> g(k.mu);
-  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  for (int i = 0; i < 4 * gevp::kKtClasses; ++i) out[i] = 0.0;
   for (const auto& r : k.recs) {
     if (cudaEventSynchronize(r.e1) != cudaSuccess) return GEVP_ERR_CUDA;
     float ms = 0.f;

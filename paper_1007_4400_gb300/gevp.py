@@ -506,13 +506,13 @@ def kernel_timing(enable: bool) -> None:
 
 def kernel_timing_read() -> dict:
     """Per kernel class: launches, total ms, algorithmic and executed flop."""
-    out = (C.c_double * 8)()
+    out = (C.c_double * 12)()
     st = load().gevp_kernel_timing_read(out)
     if st != 0:
         raise GevpError(st, "gevp_kernel_timing_read")
-    names = ("zgemm_kernel", "oz_gemm_kernel")
+    names = ("zgemm_kernel", "oz_gemm_kernel", "zgram_kernel")
     return {names[c]: {"launches": int(out[4 * c]), "ms": out[4 * c + 1], "alg_flop": out[4 * c + 2],
-                       "exec_flop": out[4 * c + 3]} for c in range(2)}
+                       "exec_flop": out[4 * c + 3]} for c in range(3)}
 
 
 def kernel_launches(device=None) -> int:

@@ -75,7 +75,7 @@ def test_kernel_timing_records_nothing_without_launches():
     gevp.kernel_timing(True)
     out = gevp.kernel_timing_read()
     gevp.kernel_timing(False)
-    assert set(out) == {"zgemm_kernel", "oz_gemm_kernel"}
+    assert set(out) == {"zgemm_kernel", "oz_gemm_kernel", "zgram_kernel"}
     for v in out.values():
         assert v["launches"] == 0 and v["ms"] == 0.0 and v["alg_flop"] == 0.0 and v["exec_flop"] == 0.0
 
