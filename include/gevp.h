@@ -241,11 +241,20 @@ gevp_status gevp_heev_small(gevp_handle h, int m, const void* G, int64_t ldg, do
 gevp_status gevp_spectral_bounds(gevp_handle h, int64_t n, const void* C, int64_t ldc, int k, int count,
                                  double* out);
 
+/* Band energy E = sum_{i<nev} lambda_i, the sum of the occupied eigenvalues of each problem
+ * (the band-structure term of the Kohn-Sham total energy whose eigenproblem is Eq. 3).
+ *   Lambda: device nprob x nev (row p = problem p, as gevp_solve_sequence writes it);
+ *   E: device nprob, E[p] summed in index order (deterministic). Enqueued on the handle's
+ *   stream; returns without waiting. */
+gevp_status gevp_band_energy(gevp_handle h, int nprob, int nev, const double* Lambda, double* E);
+
 /* Band-energy gradient for E = sum_{i<nev} lambda_i (first-order perturbation theory):
  *   GA = gE * X X^H = dE/dA * gE,   GB = -gE * X diag(Lambda) X^H = dE/dB * gE,
- * X n x nev B-orthonormal eigenvectors (ld ldx), Lambda device (nev); GA, GB n x n (ld ldg). */
+ * X n x nev B-orthonormal eigenvectors (ld ldx), Lambda device (nev), gE a DEVICE scalar
+ * (the incoming gradient, read on the device: no host synchronisation); GA, GB n x n (ld
+ * ldg). Enqueued on the handle's stream; returns without waiting. */
 gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* X, int64_t ldx,
-                                 const double* Lambda, double gE, void* GA, void* GB, int64_t ldg);
+                                 const double* Lambda, const double* gE, void* GA, void* GB, int64_t ldg);
 
 /* Entry-variation statistics between the Hamiltonians of consecutive self-consistent
  * iterations (Sec. "Matrix generation": the largest entry variation delta_{n+1} and the
@@ -336,12 +345,12 @@ gevp_status gevp_probe_peaks(gevp_handle h, double* out);
 #define GEVP_NOALLOC_MAX_ELEMS (1 << 21)
 
 /* The FP64 Chebyshev filter of gevp_chebyshev_filter (prec GEVP_PREC_FP64), for callers
- * that must not allocate device memory when they call it: code running while a CUDA
- * graph is being captured (where a cudaMalloc is illegal or would be recorded into the
- * graph), applications whose device memory belongs to a pool allocator such as
- * PyTorch's caching allocator (a library cudaMalloc/cudaFree would bypass the pool and
- * synchronise the device), and services that reserve a fixed memory budget at start-up.
- * The paper has no counterpart; it is a deployment variant of the same computation.
+ * that must not allocate device memory when they call it: applications whose device
+ * memory belongs to a pool allocator such as PyTorch's caching allocator (a library
+ * cudaMalloc/cudaFree would bypass the pool, can fail while the pool holds the free memory,
+ * and synchronises the device), and services that reserve a fixed memory budget at
+ * start-up. The paper has no counterpart; it is a deployment variant of the same
+ * computation.
  *   No handle: the work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *   stream) of the current device and the call returns without waiting for it. C, Y as in
  *   gevp_chebyshev_filter (device, row-major complex128, Y n x m overwritten in place).
@@ -349,10 +358,14 @@ gevp_status gevp_probe_peaks(gevp_handle h, double* out);
  *   blocks, is a fixed array in the library's device image: requires 2 n m <=
  *   GEVP_NOALLOC_MAX_ELEMS, else GEVP_ERR_INVALID_ARG is returned and nothing is enqueued.
  *   The first call on a device looks up the array's device address (once per device, with
- *   that device current); make that first call before any stream capture. Every call on a
- *   device shares the one array, which keeps the previous call's contents (each call
- *   writes every scratch element it reads first, so nothing needs clearing): calls whose
- *   work overlaps on the GPU (other streams, other host threads) race on it. */
+ *   that device current) and caches it for the life of the process; make that first call
+ *   before any stream capture, and do not use the entry point across a cudaDeviceReset
+ *   (the cached address would be stale). Every call on a device shares the one array,
+ *   which keeps the previous call's contents (each call writes every scratch element it
+ *   reads first, so nothing needs clearing): calls whose work overlaps on the GPU (other
+ *   streams, other host threads) race on it. If a CUDA error from earlier work is pending
+ *   on the calling thread, GEVP_ERR_CUDA is returned, the error is left pending and nothing
+ *   is enqueued. */
 gevp_status gevp_chebyshev_filter_noalloc(void* stream, int64_t n, const void* C, int64_t ldc, void* Y, int64_t ldy,
                                           int m, int degree, double lo, double hi, double s);
 
@@ -368,7 +381,9 @@ gevp_status gevp_kernel_timing(int enable);
  * BF16 real products, 36x the algorithmic at 8 digits). Waits for the recorded events. */
 gevp_status gevp_kernel_timing_read(double* out);
 
-/* Number of kernels the handle launched since creation (for launch accounting). */
+/* Number of kernels the library launched since it was loaded, process-wide: every handle,
+ * the handle-less entry points and every host thread (h is accepted for compatibility and
+ * not used). For launch accounting. */
 int64_t gevp_kernel_launches(gevp_handle h);
 
 #ifdef __cplusplus

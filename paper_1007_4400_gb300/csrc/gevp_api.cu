@@ -26,7 +26,7 @@
 using namespace gevp;
 
 namespace gevp {
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
 }
 
 struct gevp_ctx {
@@ -633,30 +633,7 @@ gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const doubl
 // Chebyshev filter on Y0 (n x ma, ld ld0) with FP64 products; returns the output buffer.
 double2* filter_fp64(gevp_ctx* h, int64_t n, const double2* C, int64_t ldc, const double2* Y0, int64_t ld0, int ma,
                      int deg, double lo, double hi, double sc, double2* B1, double2* B2, int64_t ldb) {
-  double e = 0.5 * (hi - lo), c = 0.5 * (hi + lo);
-  double sigma = e / (sc - c), sigma1 = sigma;
-  ZgemmArgs a = zg((int)n, ma, (int)n, C, ldc, 0, Y0, ld0, 0, B1, ldb, sigma1 / e);
-  a.Cin = Y0; a.ldc = ld0; a.beta = -c * sigma1 / e;
-  zgemm(a, h->split, h->split_elems, h->stream);
-  const double2* prev = Y0;
-  int64_t ldp = ld0;
-  double2* cur = B1;
-  double2* nxt = B2;
-  for (int i = 2; i <= deg; ++i) {
-    double sn = 1.0 / (2.0 / sigma1 - sigma);
-    double al = 2.0 * sn / e;
-    ZgemmArgs s = zg((int)n, ma, (int)n, C, ldc, 0, cur, ldb, 0, nxt, ldb, al);
-    s.Cin = cur; s.ldc = ldb; s.beta = -al * c;
-    s.Ein = prev; s.lde = ldp; s.gamma = -sigma * sn;
-    zgemm(s, h->split, h->split_elems, h->stream);
-    sigma = sn;
-    double2* old = cur;
-    prev = old;
-    ldp = ldb;
-    cur = nxt;
-    nxt = old;   // overwrites the step before 'cur' next time (allowed: read-then-write per element)
-  }
-  return cur;
+  return cheb_filter_fp64(n, C, ldc, Y0, ld0, ma, deg, lo, hi, sc, B1, B2, ldb, h->split, h->split_elems, h->stream);
 }
 
 gevp_status lanczos(gevp_ctx* h, int64_t n, const double2* M, int64_t ldm, int k, int count, uint64_t seed,
@@ -1048,7 +1025,7 @@ const char* gevp_version(void) { return "gevp-gb300 0.1 (sm_103a)"; }
 
 const char* gevp_last_error(gevp_handle h) { return h ? h->err.c_str() : "null handle"; }
 
-int64_t gevp_kernel_launches(gevp_handle h) { (void)h; return gevp::g_launches; }
+int64_t gevp_kernel_launches(gevp_handle h) { (void)h; return gevp::g_launches.load(); }
 
 gevp_status gevp_create(gevp_handle* out, int device, void* stream) {
   if (!out) return GEVP_ERR_INVALID_ARG;
@@ -1462,16 +1439,25 @@ gevp_status gevp_spectral_bounds(gevp_handle h, int64_t n, const void* C, int64_
   return GEVP_OK;
 }
 
+gevp_status gevp_band_energy(gevp_handle h, int nprob, int nev, const double* Lambda, double* E) {
+  if (!h || nprob < 0 || nev < 0) return GEVP_ERR_INVALID_ARG;
+  if (nprob == 0) return GEVP_OK;
+  if (!E || (nev > 0 && !Lambda)) return GEVP_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  gevp::band_energy(nprob, nev, Lambda, E, h->stream);
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
 gevp_status gevp_energy_backward(gevp_handle h, int64_t n, int nev, const void* X, int64_t ldx, const double* Lambda,
-                                 double gE, void* GA, void* GB, int64_t ldg) {
+                                 const double* gE, void* GA, void* GB, int64_t ldg) {
   if (!h || n < 0 || nev < 0 || nev > n) return GEVP_ERR_INVALID_ARG;
   if (n == 0) return GEVP_OK;
-  if (!X || !Lambda || !GA || !GB || bad_ld(ldx, nev) || bad_ld(ldg, n)) return GEVP_ERR_INVALID_ARG;
+  if (!X || !Lambda || !gE || !GA || !GB || bad_ld(ldx, nev) || bad_ld(ldg, n)) return GEVP_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   TRY(ensure(h, n, std::max(nev, 1)));
   gevp::energy_backward_ws(n, nev, (const double2*)X, ldx, Lambda, gE, (double2*)GA, (double2*)GB, ldg, h->T,
                            h->split, h->split_elems, h->stream);
-  CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return GEVP_OK;
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 
@@ -58,6 +59,10 @@ struct ZgemmArgs {
 };
 
 void zgemm(const ZgemmArgs& a, double2* split_ws, size_t split_ws_elems, cudaStream_t s);
+// Scaled Chebyshev filter with FP64 products (see zgemm.cu); returns B1 or B2.
+double2* cheb_filter_fp64(int64_t n, const double2* C, int64_t ldc, const double2* Y0, int64_t ld0, int ma, int deg,
+                          double lo, double hi, double sc, double2* B1, double2* B2, int64_t ldb, double2* split_ws,
+                          size_t split_elems, cudaStream_t s);
 // Simple helper for the common case.
 ZgemmArgs zg(int M, int N, int K, const double2* A, int64_t lda, int opA,
              const double2* B, int64_t ldb, int opB, double2* D, int64_t ldd, double alpha = 1.0);
@@ -90,6 +95,10 @@ void zshift_diag(int64_t n, double2* A, int64_t lda, double sh, cudaStream_t s);
 void zero_lower(int64_t n, double2* A, int64_t lda, cudaStream_t s);        // strict lower <- 0
 void hermitize_lower(int64_t n, double2* C, int64_t ldc, cudaStream_t s);   // upper <- conj(lower), real diag
 void hermitize_avg(int64_t n, double2* C, int64_t ldc, cudaStream_t s);     // C <- (C + C^H)/2
+// lower triangle scaled by sign * (*scale) (device scalar), then upper <- conj(lower)
+void hermitize_scale_lower(int64_t n, double2* C, int64_t ldc, const double* scale, double sign, cudaStream_t s);
+// E[p] = sum of lam[p * nev + 0 .. nev - 1] in index order (device arrays)
+void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t s);
 void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s);        // strict upper <- 0
 void zcopy2d(int64_t rows, int64_t cols, const double2* src, int64_t lds, double2* dst, int64_t ldd, cudaStream_t s);
 void zset_identity(int64_t rows, int64_t cols, double2* A, int64_t lda, cudaStream_t s);
@@ -162,9 +171,9 @@ bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* 
                    int64_t ldl, int* info, cudaStream_t s);
 
 // ---------------------------------------------------------------- backward
-// GA = gE X X^H, GB = -gE X diag(lam) X^H (lower tiles by GEMM, then Hermitian completion).
-// XL: n x nev scratch.
-void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const double* lam, double gE,
+// GA = gE X X^H, GB = -gE X diag(lam) X^H (lower tiles by GEMM, then Hermitian completion
+// scaled by the device scalar *gE). XL: n x nev scratch.
+void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const double* lam, const double* gE,
                         double2* GA, double2* GB, int64_t ldg, double2* XL, double2* split, size_t split_elems,
                         cudaStream_t s);
 
@@ -328,7 +337,9 @@ BatchPlan*& ctx_batch(gevp_ctx* h);
 void probe_peaks(double* fp64_fma_tflops, double* fp64_dmma_tflops, double* fp32_fma_tflops, cudaStream_t s);
 
 // ---------------------------------------------------------------- launch accounting
-extern int64_t g_launches;
+// process-wide count of kernel launches (all handles, the handle-less entry points, all
+// host threads)
+extern std::atomic<int64_t> g_launches;
 #define LAUNCH_NOTE(k) (::gevp::g_launches += (k))
 
 // ---------------------------------------------------------------- live kernel timing

@@ -52,6 +52,32 @@ __global__ void hermitize_lower_kernel(int64_t n, double2* C, int64_t ldc) {
   }
 }
 
+// lower triangle scaled by sign * (*scale) (a device scalar), upper <- conj(lower), real diagonal
+__global__ void hermitize_scale_lower_kernel(int64_t n, double2* C, int64_t ldc, const double* scale, double sign) {
+  const double f = sign * scale[0];
+  int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / n, j = e % n;
+    if (j > i) continue;
+    double2 v = zscale(C[i * ldc + j], f);
+    if (j == i) {
+      C[i * ldc + i] = make_double2(v.x, 0.0);
+    } else {
+      C[i * ldc + j] = v;
+      C[j * ldc + i] = zconj(v);
+    }
+  }
+}
+
+// E[p] = sum_i lam[p * nev + i], summed in index order (one thread per problem)
+__global__ void band_energy_kernel(int nprob, int nev, const double* lam, double* E) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  double s = 0.0;
+  for (int i = 0; i < nev; ++i) s += lam[(int64_t)p * nev + i];
+  E[p] = s;
+}
+
 __global__ void hermitize_avg_kernel(int64_t n, double2* C, int64_t ldc) {
   int64_t total = n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -158,6 +184,14 @@ void zero_lower(int64_t n, double2* A, int64_t lda, cudaStream_t s) {
 }
 void hermitize_lower(int64_t n, double2* C, int64_t ldc, cudaStream_t s) {
   hermitize_lower_kernel<<<grid_for(n * n), kThreads, 0, s>>>(n, C, ldc);
+  LAUNCH_NOTE(1);
+}
+void hermitize_scale_lower(int64_t n, double2* C, int64_t ldc, const double* scale, double sign, cudaStream_t s) {
+  hermitize_scale_lower_kernel<<<grid_for(n * n), kThreads, 0, s>>>(n, C, ldc, scale, sign);
+  LAUNCH_NOTE(1);
+}
+void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t s) {
+  band_energy_kernel<<<(nprob + 127) / 128, 128, 0, s>>>(nprob, nev, lam, E);
   LAUNCH_NOTE(1);
 }
 void hermitize_avg(int64_t n, double2* C, int64_t ldc, cudaStream_t s) {

@@ -199,21 +199,23 @@ void gram_scale(int m, double2* W, int64_t ldw, double* dscale, cudaStream_t s) 
   LAUNCH_NOTE(1);
 }
 
-void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const double* lam, double gE, double2* GA,
-                        double2* GB, int64_t ldg, double2* XL, double2* split, size_t split_elems, cudaStream_t s) {
-  // GA = gE X X^H, GB = -gE (X diag(lam)) X^H ; lower tiles then Hermitian completion
-  ZgemmArgs a = zg((int)n, (int)n, nev, X, ldx, 0, X, ldx, 1, GA, ldg, gE);
+void energy_backward_ws(int64_t n, int nev, const double2* X, int64_t ldx, const double* lam, const double* gE,
+                        double2* GA, double2* GB, int64_t ldg, double2* XL, double2* split, size_t split_elems,
+                        cudaStream_t s) {
+  // GA = gE X X^H, GB = -gE (X diag(lam)) X^H ; lower tiles, then the Hermitian completion
+  // applies the incoming gradient gE (a device scalar: no host synchronisation)
+  ZgemmArgs a = zg((int)n, (int)n, nev, X, ldx, 0, X, ldx, 1, GA, ldg);
   a.triD = 1;
   zgemm(a, split, split_elems, s);
-  hermitize_lower(n, GA, ldg, s);
+  hermitize_scale_lower(n, GA, ldg, gE, 1.0, s);
   int64_t total = n * nev;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   scale_rows_by_lam_kernel<<<blocks, 256, 0, s>>>(n, nev, X, ldx, lam, XL);
   LAUNCH_NOTE(1);
-  ZgemmArgs b = zg((int)n, (int)n, nev, XL, nev, 0, X, ldx, 1, GB, ldg, -gE);
+  ZgemmArgs b = zg((int)n, (int)n, nev, XL, nev, 0, X, ldx, 1, GB, ldg);
   b.triD = 1;
   zgemm(b, split, split_elems, s);
-  hermitize_lower(n, GB, ldg, s);
+  hermitize_scale_lower(n, GB, ldg, gE, -1.0, s);
 }
 
 void probe_peaks(double* fp64_fma_tflops, double* fp64_dmma_tflops, double* fp32_fma_tflops, cudaStream_t s) {

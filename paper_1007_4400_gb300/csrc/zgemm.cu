@@ -247,4 +247,37 @@ void zgemm(const ZgemmArgs& in, double2* split_ws, size_t split_ws_elems, cudaSt
   }
 }
 
+// Scaled Chebyshev filter (Zhou, Saad, Tiago & Chelikowsky 2006) with FP64 products: Y0
+// (n x ma, ld ld0) through deg steps of the three-term recurrence, each step one complex
+// GEMM with the recurrence fused into its epilogue, ping-ponging between B1 and B2 (ld
+// ldb); returns the buffer holding the result. split_ws may be null (no split-K).
+double2* cheb_filter_fp64(int64_t n, const double2* C, int64_t ldc, const double2* Y0, int64_t ld0, int ma, int deg,
+                          double lo, double hi, double sc, double2* B1, double2* B2, int64_t ldb, double2* split_ws,
+                          size_t split_elems, cudaStream_t s) {
+  double e = 0.5 * (hi - lo), c = 0.5 * (hi + lo);
+  double sigma = e / (sc - c), sigma1 = sigma;
+  ZgemmArgs a = zg((int)n, ma, (int)n, C, ldc, 0, Y0, ld0, 0, B1, ldb, sigma1 / e);
+  a.Cin = Y0; a.ldc = ld0; a.beta = -c * sigma1 / e;
+  zgemm(a, split_ws, split_elems, s);
+  const double2* prev = Y0;
+  int64_t ldp = ld0;
+  double2* cur = B1;
+  double2* nxt = B2;
+  for (int i = 2; i <= deg; ++i) {
+    double sn = 1.0 / (2.0 / sigma1 - sigma);
+    double al = 2.0 * sn / e;
+    ZgemmArgs g = zg((int)n, ma, (int)n, C, ldc, 0, cur, ldb, 0, nxt, ldb, al);
+    g.Cin = cur; g.ldc = ldb; g.beta = -al * c;
+    g.Ein = prev; g.lde = ldp; g.gamma = -sigma * sn;
+    zgemm(g, split_ws, split_elems, s);
+    sigma = sn;
+    double2* old = cur;
+    prev = old;
+    ldp = ldb;
+    cur = nxt;
+    nxt = old;   // overwrites the step before 'cur' next time (allowed: read-then-write per element)
+  }
+  return cur;
+}
+
 }  // namespace gevp

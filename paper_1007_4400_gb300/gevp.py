@@ -111,7 +111,8 @@ def load(build_if_missing: bool = True):
         L.gevp_rayleigh_ritz.argtypes = [vp, i64, i32, vp, i64, vp, i64, vp, i64, vp, vp]
         L.gevp_heev_small.argtypes = [vp, i32, vp, i64, vp, vp, i64]
         L.gevp_spectral_bounds.argtypes = [vp, i64, vp, i64, i32, i32, C.POINTER(f64)]
-        L.gevp_energy_backward.argtypes = [vp, i64, i32, vp, i64, vp, f64, vp, vp, i64]
+        L.gevp_energy_backward.argtypes = [vp, i64, i32, vp, i64, vp, vp, vp, vp, i64]
+        L.gevp_band_energy.argtypes = [vp, i32, i32, vp, vp]
         L.gevp_probe_peaks.argtypes = [vp, C.POINTER(f64)]
         L.gevp_matrix_variation.argtypes = [vp, i64, vp, i64, vp, i64, i32, C.POINTER(f64), C.POINTER(f64),
                                             C.POINTER(i64), vp]
@@ -127,7 +128,7 @@ def load(build_if_missing: bool = True):
         L.gevp_kernel_launches.restype = i64
         for name in ("gevp_create", "gevp_destroy", "gevp_set_stream", "gevp_reduce", "gevp_solve_sequence",
                      "gevp_solve_sequence_host", "gevp_solve_batched", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
-                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_probe_peaks",
+                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_band_energy", "gevp_probe_peaks",
                      "gevp_matrix_variation", "gevp_deviation_angles", "gevp_assign_min_cost",
                      "gevp_zgemm_emulated", "gevp_reduce_emulated", "gevp_kernel_timing",
                      "gevp_kernel_timing_read"):
@@ -413,18 +414,35 @@ def spectral_bounds(Cm: torch.Tensor, k: int = 32, count: int = 0):
     return list(out)
 
 
-def energy_backward(X: torch.Tensor, Lambda: torch.Tensor, gE: float = 1.0):
-    """(GA, GB) = (gE X X^H, -gE X diag(Lambda) X^H)."""
+def energy_backward(X: torch.Tensor, Lambda: torch.Tensor, gE=1.0):
+    """(GA, GB) = (gE X X^H, -gE X diag(Lambda) X^H). gE: a number or a one-element float64
+    tensor on X's device (read there by the library, no host synchronisation)."""
     _mat(X, "X")
     _mat(Lambda, "Lambda", torch.float64)
     h = _handle(X.device)
     n, nev = X.shape
+    if isinstance(gE, torch.Tensor):
+        g = gE.detach().to(device=X.device, dtype=torch.float64).reshape(1).contiguous()
+    else:
+        g = torch.tensor([float(gE)], dtype=torch.float64, device=X.device)
+    lam = Lambda.contiguous()
     GA = torch.empty((n, n), dtype=torch.complex128, device=X.device)
     GB = torch.empty_like(GA)
-    st = load().gevp_energy_backward(h, n, nev, _ptr(X), X.stride(0), _ptr(Lambda.contiguous()), float(gE),
-                                     _ptr(GA), _ptr(GB), n)
+    st = load().gevp_energy_backward(h, n, nev, _ptr(X), X.stride(0), _ptr(lam), _ptr(g), _ptr(GA), _ptr(GB), n)
     _check(st, h)
     return GA, GB
+
+
+def band_energy_of(Lambda: torch.Tensor) -> torch.Tensor:
+    """E[p] = sum of row p of Lambda (nprob x nev, device), computed by the library."""
+    _mat(Lambda, "Lambda", torch.float64)
+    lam = Lambda.contiguous()
+    h = _handle(lam.device)
+    nprob, nev = lam.shape
+    E = torch.empty((nprob,), dtype=torch.float64, device=lam.device)
+    st = load().gevp_band_energy(h, nprob, nev, _ptr(lam), _ptr(E))
+    _check(st, h)
+    return E
 
 
 def matrix_variation(A_new: torch.Tensor, A_old: torch.Tensor, thresholds=(0.1,), want_mask: bool = False):
@@ -534,12 +552,12 @@ class GevpEnergy(torch.autograd.Function):
         r = solve_sequence([A], B, nev, **(opts or {}))
         ctx.save_for_backward(r.X, r.Lambda[0])
         ctx.result = r
-        return r.Lambda[0].sum()
+        return band_energy_of(r.Lambda[:1])[0]
 
     @staticmethod
     def backward(ctx, gE):
         X, lam = ctx.saved_tensors
-        GA, GB = energy_backward(X, lam, float(gE))
+        GA, GB = energy_backward(X, lam, gE)
         return GA, GB, None, None
 
 
