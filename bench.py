@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--seq-steps", type=int, default=10, help="kpoint_batch workload: problems per k-point")
     p.add_argument("--reduce-slices", type=int, default=8,
                    help="digits of the emulated FP64 products of the reduction (0: FP64 pipe)")
-    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki", "seq_small"],
+    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki", "seq_small", "cholqr"],
                    default=None,
                    help="run only a few launches of one kernel (n 2048, m 140) for ncu captures")
     return p.parse_args()
@@ -91,6 +91,22 @@ def kernel_case(args):
         r = gevp.solve_sequence([a.to(dev) for a in seq.A], seq.B.to(dev), 64, nex=24, filter_prec="fp32")
         torch.cuda.synchronize()
         print(f"kernel case seq_small done: status {r.status}, max residual {float(r.resid.max()):.2e}")
+        return 0
+    if args.kernel_case == "cholqr":
+        # the bench shape of the tall-skinny kernels: CholQR2 of a 2048 x 140 block with
+        # columns scaled over three decades (Gram kernel, cluster Cholesky-inverse, product)
+        # and one Rayleigh-Ritz projection on the result
+        n, m = 2048, 140
+        g = torch.Generator(device=dev).manual_seed(5)
+        Y = torch.randn((n, m), dtype=torch.complex128, device=dev, generator=g)
+        Y = Y * torch.logspace(0, 3, m, dtype=torch.float64, device=dev)[None, :]
+        G = torch.randn((n, n), dtype=torch.complex128, device=dev, generator=g)
+        C = (0.5 * (G + G.conj().T) * (25.0 / n ** 0.5)).contiguous()
+        Q = gevp.cholqr2(Y)
+        Q = gevp.cholqr2(Q)
+        gevp.rayleigh_ritz(C, Q)
+        torch.cuda.synchronize()
+        print(f"kernel case cholqr done: n={n} m={m}")
         return 0
     if args.kernel_case == "ozaki":
         # the emulated FP64 product D = A B^H (n = 2048, 8 digits) and the reduction to

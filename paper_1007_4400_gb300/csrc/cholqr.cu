@@ -111,9 +111,11 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
   __shared__ double2 cs[kCholInvMax / 8]; // own rows' A[i, j] / a_jj
   __shared__ double dsc[kCholInvMax];     // D
   __shared__ double piv[kCholInvMax];     // sqrt(a_jj)
+  __shared__ double2 pinfo[kCholInvMax / 8];   // own rows: (pivot a_ii, rsqrt(a_ii)) once final
   __shared__ double2* rA[P];
   __shared__ double2* rS[P];
-  __shared__ double apiv, inv2;
+  __shared__ double2* rPI[P];
+  __shared__ double apiv;
   const int tid = threadIdx.x;
   const int rank = (int)cl.block_rank();
   const int R = (m + P - 1) / P;
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
   if (tid < P) {
     rA[tid] = cl.map_shared_rank(Arow, tid);
     rS[tid] = cl.map_shared_rank(Srow, tid);
+    rPI[tid] = cl.map_shared_rank(pinfo, tid);
   }
   for (int i = tid; i < m; i += CT) {
     const double v = W[(int64_t)i * ldw + i].x;
@@ -139,17 +142,40 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
     Arow[e] = a;
     Srow[e] = s;
   }
+  // the first pivot is final from the start: its owner (rank 0, local row 0; this thread
+  // wrote that entry above) prepares its reciprocal square root
+  if (rank == 0 && tid == 0) {
+    const double a0 = Arow[0].x;
+    pinfo[0] = make_double2(a0, a0 > 0.0 ? rsqrt(a0) : 0.0);
+  }
   cl.sync();
   bool failed = false;
   for (int j = 0; j < m; ++j) {
     const int oj = j % P, tjj = j / P;
+    // own rows below the pivot: i = rank + P t > j, t in [t0, t1)
+    const int t0 = j >= rank ? (j - rank) / P + 1 : 0;
+    int t1 = R;
+    while (t1 > t0 && rank + P * (t1 - 1) >= m) --t1;
+    const int nr = t1 - t0;
+    // gather column j and row j of the inverse (raw values, final after step j - 1); the
+    // threads of own rows also form the row's multiplier -A[i][j] / a_jj from the pivot's
+    // reciprocal square root, prepared by the pivot's owner when it became final
     for (int l = tid; l < m; l += CT) {
       if (l > j) {
-        cbuf[l] = rA[l % P][(l / P) * m + j];
+        const double2 c = rA[l % P][(l / P) * m + j];
+        cbuf[l] = c;
+        if (l % P == rank) {
+          const double ri = rPI[oj][tjj].y;
+          cs[l / P - t0] = zscale(c, -(ri * ri));
+        }
       } else {
         xbuf[l] = rS[oj][tjj * m + l];
-        if (l == j) apiv = rA[oj][tjj * m + j].x;
       }
+    }
+    if (tid == 0) {
+      const double2 pv = rPI[oj][tjj];
+      apiv = pv.x;
+      piv[j] = pv.x * pv.y;
     }
     __syncthreads();
     const double a = apiv;   // the same value in every CTA: a uniform decision
@@ -158,31 +184,19 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
       failed = true;
       break;
     }
-    if (tid == 0) {
-      const double ri = rsqrt(a);
-      piv[j] = a * ri;
-      inv2 = ri * ri;
-    }
-    __syncthreads();
-    // own rows below the pivot: i = rank + P t > j
-    const int t0 = j >= rank ? (j - rank) / P + 1 : 0;
-    int t1 = R;
-    while (t1 > t0 && rank + P * (t1 - 1) >= m) --t1;
-    const int nr = t1 - t0;
-    if (tid < nr) cs[tid] = zscale(cbuf[rank + P * (t0 + tid)], inv2);
-    __syncthreads();
     for (int idx = tid; idx < nr * m; idx += CT) {
       const int tt = idx / m, e = idx % m, t = t0 + tt, i = rank + P * t;
       if (e > i) continue;
       const double2 li = cs[tt];
       if (e <= j) {
         double2 v = Srow[t * m + e];
-        zfma(v, zscale(li, -1.0), xbuf[e]);
+        zfma(v, li, xbuf[e]);
         Srow[t * m + e] = v;
       } else {
         double2 v = Arow[t * m + e];
-        zfma(v, zscale(li, -1.0), zconj(cbuf[e]));
+        zfma(v, li, zconj(cbuf[e]));
         Arow[t * m + e] = v;
+        if (e == i && i == j + 1) pinfo[t] = make_double2(v.x, v.x > 0.0 ? rsqrt(v.x) : 0.0);
       }
     }
     cl.sync();

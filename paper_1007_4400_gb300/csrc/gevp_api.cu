@@ -300,6 +300,15 @@ gevp_status sync_read(gevp_ctx* h, const void* dsrc, void* hdst, size_t bytes) {
   return GEVP_OK;
 }
 
+// two device-to-host reads with one synchronisation
+gevp_status sync_read2(gevp_ctx* h, const void* d1, void* h1, size_t b1, const void* d2, void* h2, size_t b2) {
+  CK(cudaMemcpyAsync(h1, d1, b1, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h2, d2, b2, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
 // ---------------------------------------------------------------- building blocks
 gevp_status factor_B(gevp_ctx* h, int64_t n, const double2* B, int64_t ldb, int64_t* info_out) {
   CK(cudaMemsetAsync(h->info, 0, sizeof(int), h->stream));
@@ -604,17 +613,24 @@ gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_
   return GEVP_ERR_NOT_HPD;
 }
 
+// Out = C Qa (n x ma, ld of the block), emulated when C's digits are held
+gevp_status times_C(gevp_ctx* h, int64_t n, int ma, const double2* C, int64_t ldc, const double2* Qa, double2* Out) {
+  const int64_t ld = h->cap_m;
+  if (h->oz_slices > 0 && h->ozC_src == (const void*)C) {
+    TRY(oz_times_block(h, h->ozC, n, ma, Qa, ld, Out, ld));
+  } else {
+    ZgemmArgs w = zg((int)n, ma, (int)n, C, ldc, 0, Qa, ld, 0, Out, ld);
+    zgemm(w, h->split, h->split_elems, h->stream);
+  }
+  return GEVP_OK;
+}
+
 // Rayleigh-Ritz on the active columns Q[:, nlock:nlock+ma]; updates Q, W, theta, res there.
 gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const double2* C, int64_t ldc,
                           int refine, gevp_stats* st) {
   const int64_t ld = h->cap_m;
   double2* Qa = h->Q + nlock;
-  if (h->oz_slices > 0 && h->ozC_src == (const void*)C) {
-    TRY(oz_times_block(h, h->ozC, n, ma, Qa, ld, h->Wt, ld));
-  } else {
-    ZgemmArgs w = zg((int)n, ma, (int)n, C, ldc, 0, Qa, ld, 0, h->Wt, ld);
-    zgemm(w, h->split, h->split_elems, h->stream);
-  }
+  TRY(times_C(h, n, ma, C, ldc, Qa, h->Wt));
   // G = Q^H C Q is Hermitian: its lower tiles only, both triangles written
   zgram(n, ma, ma, Qa, ld, h->Wt, ld, h->G, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
   heev_small(ma, h->G, ma, h->theta + nlock, h->Zs, ma, h->hw, refine, h->stream);
@@ -708,7 +724,7 @@ double predicted_max_res(const SolveState& S, double lo, double hi, double tolC,
 gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, const double2* B, int64_t ldb,
                       int nev, int m, bool warm, const gevp_opts& o, int prob_index, Timer& tm, gevp_stats* st,
                       double* Lam_out, double2* X_out, int64_t ldx, double* res_out, const double* pre = nullptr,
-                      bool tc_ready = false) {
+                      bool tc_ready = false, bool prev_ritz = false) {
   const int64_t ld = h->cap_m;
   SolveState S;
   S.m = m;
@@ -762,11 +778,26 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
     tm.mark(PH_ORTH);
   }
-  if (warm || m == n) {
-    // warm start, or a block that spans the whole space (then this projection is exact)
+  // estimate: theta and res are the Rayleigh quotients and residuals of the unrotated
+  // block (not Ritz pairs of a projection); nothing is locked on them
+  bool estimate = false;
+  if (warm && prev_ritz && m < n) {
+    // warm start: the previous problem's Ritz block against the new C. The first filter acts
+    // on its span, which a Rayleigh-Ritz rotation would not change, so only W = C Q is
+    // formed: theta_i = Re(q_i^H W_i) and ||W_i - theta_i q_i|| give the degree and the
+    // interval, and R = W - Q Theta drives the residual-corrected low-precision filter
+    TRY(times_C(h, n, m, h->C, n, h->Q, h->W));
+    column_bnorms(n, m, h->Q, ld, h->W, ld, h->partial, h->theta, h->stream);
+    resid_norms(n, m, h->W, ld, h->Q, ld, h->theta, h->res, h->partial, h->stream);
+    TRY(sync_read2(h, h->theta, S.theta.data(), m * sizeof(double), h->res, S.res.data(), m * sizeof(double)));
+    if (st) st->flops_fp64 += 8.0 * (double)n * n * m;
+    S.have_theta = true;
+    estimate = true;
+    tm.mark(PH_RR);
+  } else if (warm || m == n) {
+    // a block that spans the whole space (then this projection is exact)
     TRY(rayleigh_ritz(h, n, 0, m, h->C, n, o.refine_iters, st));
-    TRY(sync_read(h, h->theta, S.theta.data(), m * sizeof(double)));
-    TRY(sync_read(h, h->res, S.res.data(), m * sizeof(double)));
+    TRY(sync_read2(h, h->theta, S.theta.data(), m * sizeof(double), h->res, S.res.data(), m * sizeof(double)));
     S.have_theta = true;
     tm.mark(PH_RR);
   }
@@ -776,7 +807,7 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   bool converged = false;
   int deg_cap = o.deg_max;   // lowered when the FP32-class filter reaches its floor
   for (int it = 0;; ++it) {
-    if (S.have_theta) {
+    if (S.have_theta && !estimate) {
       while (S.nlock < nev && S.res[S.nlock] <= tolC) S.nlock++;
     }
     if (S.nlock >= nev) {
@@ -848,8 +879,11 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     // ---- filter the active columns
     int ma = m - S.nlock;
     double hi = S.upper;
-    double lo = S.have_theta ? S.theta[m - 1] : S.a_est;
-    double sc = S.have_theta ? std::min(S.theta[0], S.lower_est) : S.lower_est;
+    // Ritz values are ascending; the estimates of a warm start need not be
+    const double th_lo = S.have_theta ? *std::min_element(S.theta.begin(), S.theta.end()) : 0.0;
+    const double th_hi = S.have_theta ? *std::max_element(S.theta.begin(), S.theta.end()) : 0.0;
+    double lo = S.have_theta ? th_hi : S.a_est;
+    double sc = S.have_theta ? std::min(th_lo, S.lower_est) : S.lower_est;
     if (!(lo > sc + 1e-3 * (hi - sc))) lo = sc + 0.5 * (hi - sc);
     if (!(hi > lo)) hi = lo + 1e-3 * S.normC + 1e-300;
     const int cap = std::max(o.deg_min, std::min(deg_cap, range_degree_cap(sc, lo, hi, prec)));
@@ -881,10 +915,11 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st, o.seed + 31ull * it + 7ull * prob_index));
     tm.mark(PH_ORTH);
     TRY(rayleigh_ritz(h, n, S.nlock, ma, h->C, n, o.refine_iters, st));
-    TRY(sync_read(h, h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double)));
-    TRY(sync_read(h, h->res + S.nlock, S.res.data() + S.nlock, ma * sizeof(double)));
+    TRY(sync_read2(h, h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double), h->res + S.nlock,
+                   S.res.data() + S.nlock, ma * sizeof(double)));
     tm.mark(PH_RR);
     S.have_theta = true;
+    estimate = false;
     if (st) st->outer_iters++;
     double mr = 0;
     for (int i = S.nlock; i < nev; ++i) mr = std::max(mr, S.res[i]);
@@ -1207,6 +1242,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
       have_pre = true;
     }
     bool warm = false;
+    bool prev_ritz = false;   // Q is the Ritz block the previous problem returned, unchanged
     if (!o.cold_start && !refresh) {
       if (l == 0 && X_prev) {
         // seed from the caller's vectors: Y0[:, :kprev] = L^H X_prev, rest random
@@ -1219,6 +1255,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
       } else if (warm_ok) {
         if (refactor) TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
         warm = true;
+        prev_ritz = !refactor;
       }
     }
     gevp_status s = solve_one(h, n, Al, lda, Bl, ldb, nev, m, warm, o, l, tm,
@@ -1227,7 +1264,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
                                                  : (l == nprob - 1 ? (double2*)X : nullptr)))
                                 : nullptr,
                               ldx, resid + (int64_t)l * nev, used_pre ? pre_hb : nullptr,
-                              used_pre && o.filter_prec != GEVP_PREC_FP64);
+                              used_pre && o.filter_prec != GEVP_PREC_FP64, prev_ritz);
     if (s != GEVP_OK && s != GEVP_ERR_NO_CONVERGENCE) return s;
     if (s == GEVP_ERR_NO_CONVERGENCE) overall = s;
     warm_ok = true;

@@ -163,3 +163,35 @@ def test_energy_backward_parity(cuda, orc, n, nev):
     GAr, GBr = orc.energy_grad(X, lam, 0.7)
     assert relmax(GA.cpu().numpy(), GAr) < 1e-13
     assert relmax(GB.cpu().numpy(), GBr) < 1e-13
+
+
+def test_energy_backward_device_scalar_gradient(cuda, orc):
+    """The incoming gradient is read on the device (a one-element tensor): the same result
+    as the oracle's gradient scaled by it, negative and zero scales included."""
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(711)
+    n, nev = 150, 11
+    X = crandn(rng, n, nev)
+    lam = np.sort(rng.uniform(-2, 5, nev))
+    GA1, GB1 = orc.energy_grad(X, lam, 1.0)
+    for g in (-1.75, 0.0, 3.0):
+        gE = torch.tensor([g], dtype=torch.float64, device=cuda)
+        GA, GB = gevp.energy_backward(T(X, cuda), T(lam, cuda), gE)
+        GAr, GBr = orc.energy_grad(X, lam, g)
+        tol = 1e-13 * max(1.0, abs(g))
+        assert np.abs(GA.cpu().numpy() - GAr).max() <= tol * np.abs(GA1).max()
+        assert np.abs(GB.cpu().numpy() - GBr).max() <= tol * np.abs(GB1).max()
+
+
+def test_band_energy_sums_in_index_order(cuda):
+    """gevp_band_energy: E[p] = sum of row p of Lambda, summed in index order (bit-exact
+    against the same sequential sum on the host), empty rows give 0."""
+    import functools
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(712)
+    lam = rng.uniform(-2, 50, (5, 37)) * 10.0 ** rng.integers(-8, 8, (5, 37))
+    E = gevp.band_energy_of(T(lam, cuda)).cpu().numpy()
+    for p in range(lam.shape[0]):
+        assert E[p] == functools.reduce(lambda a, b: a + b, lam[p].tolist(), 0.0)
+    E0 = gevp.band_energy_of(torch.zeros((3, 0), dtype=torch.float64, device=cuda)).cpu().numpy()
+    assert np.array_equal(E0, np.zeros(3))
