@@ -724,7 +724,7 @@ double predicted_max_res(const SolveState& S, double lo, double hi, double tolC,
 gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, const double2* B, int64_t ldb,
                       int nev, int m, bool warm, const gevp_opts& o, int prob_index, Timer& tm, gevp_stats* st,
                       double* Lam_out, double2* X_out, int64_t ldx, double* res_out, const double* pre = nullptr,
-                      bool tc_ready = false, bool prev_ritz = false) {
+                      bool tc_ready = false) {
   const int64_t ld = h->cap_m;
   SolveState S;
   S.m = m;
@@ -778,24 +778,11 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
     tm.mark(PH_ORTH);
   }
-  // estimate: theta and res are the Rayleigh quotients and residuals of the unrotated
-  // block (not Ritz pairs of a projection); nothing is locked on them
-  bool estimate = false;
-  if (warm && prev_ritz && m < n) {
-    // warm start: the previous problem's Ritz block against the new C. The first filter acts
-    // on its span, which a Rayleigh-Ritz rotation would not change, so only W = C Q is
-    // formed: theta_i = Re(q_i^H W_i) and ||W_i - theta_i q_i|| give the degree and the
-    // interval, and R = W - Q Theta drives the residual-corrected low-precision filter
-    TRY(times_C(h, n, m, h->C, n, h->Q, h->W));
-    column_bnorms(n, m, h->Q, ld, h->W, ld, h->partial, h->theta, h->stream);
-    resid_norms(n, m, h->W, ld, h->Q, ld, h->theta, h->res, h->partial, h->stream);
-    TRY(sync_read2(h, h->theta, S.theta.data(), m * sizeof(double), h->res, S.res.data(), m * sizeof(double)));
-    if (st) st->flops_fp64 += 8.0 * (double)n * n * m;
-    S.have_theta = true;
-    estimate = true;
-    tm.mark(PH_RR);
-  } else if (warm || m == n) {
-    // a block that spans the whole space (then this projection is exact)
+  if (warm || m == n) {
+    // warm start (the Rayleigh-Ritz pairs of the start block against this C: its residual
+    // R = C Q - Q Theta, which drives the corrected low-precision filter, then has no
+    // component inside span Q), or a block that spans the whole space (then this
+    // projection is exact)
     TRY(rayleigh_ritz(h, n, 0, m, h->C, n, o.refine_iters, st));
     TRY(sync_read2(h, h->theta, S.theta.data(), m * sizeof(double), h->res, S.res.data(), m * sizeof(double)));
     S.have_theta = true;
@@ -807,7 +794,7 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
   bool converged = false;
   int deg_cap = o.deg_max;   // lowered when the FP32-class filter reaches its floor
   for (int it = 0;; ++it) {
-    if (S.have_theta && !estimate) {
+    if (S.have_theta) {
       while (S.nlock < nev && S.res[S.nlock] <= tolC) S.nlock++;
     }
     if (S.nlock >= nev) {
@@ -879,11 +866,8 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
     // ---- filter the active columns
     int ma = m - S.nlock;
     double hi = S.upper;
-    // Ritz values are ascending; the estimates of a warm start need not be
-    const double th_lo = S.have_theta ? *std::min_element(S.theta.begin(), S.theta.end()) : 0.0;
-    const double th_hi = S.have_theta ? *std::max_element(S.theta.begin(), S.theta.end()) : 0.0;
-    double lo = S.have_theta ? th_hi : S.a_est;
-    double sc = S.have_theta ? std::min(th_lo, S.lower_est) : S.lower_est;
+    double lo = S.have_theta ? S.theta[m - 1] : S.a_est;
+    double sc = S.have_theta ? std::min(S.theta[0], S.lower_est) : S.lower_est;
     if (!(lo > sc + 1e-3 * (hi - sc))) lo = sc + 0.5 * (hi - sc);
     if (!(hi > lo)) hi = lo + 1e-3 * S.normC + 1e-300;
     const int cap = std::max(o.deg_min, std::min(deg_cap, range_degree_cap(sc, lo, hi, prec)));
@@ -919,7 +903,6 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
                    S.res.data() + S.nlock, ma * sizeof(double)));
     tm.mark(PH_RR);
     S.have_theta = true;
-    estimate = false;
     if (st) st->outer_iters++;
     double mr = 0;
     for (int i = S.nlock; i < nev; ++i) mr = std::max(mr, S.res[i]);
@@ -1242,7 +1225,6 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
       have_pre = true;
     }
     bool warm = false;
-    bool prev_ritz = false;   // Q is the Ritz block the previous problem returned, unchanged
     if (!o.cold_start && !refresh) {
       if (l == 0 && X_prev) {
         // seed from the caller's vectors: Y0[:, :kprev] = L^H X_prev, rest random
@@ -1255,7 +1237,6 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
       } else if (warm_ok) {
         if (refactor) TRY(orthonormalize(h, n, 0, h->Y1, ld, m, h->Q, ld, st));
         warm = true;
-        prev_ritz = !refactor;
       }
     }
     gevp_status s = solve_one(h, n, Al, lda, Bl, ldb, nev, m, warm, o, l, tm,
@@ -1264,7 +1245,7 @@ gevp_status gevp_solve_sequence(gevp_handle h, int nprob, int64_t n, const void*
                                                  : (l == nprob - 1 ? (double2*)X : nullptr)))
                                 : nullptr,
                               ldx, resid + (int64_t)l * nev, used_pre ? pre_hb : nullptr,
-                              used_pre && o.filter_prec != GEVP_PREC_FP64, prev_ritz);
+                              used_pre && o.filter_prec != GEVP_PREC_FP64);
     if (s != GEVP_OK && s != GEVP_ERR_NO_CONVERGENCE) return s;
     if (s == GEVP_ERR_NO_CONVERGENCE) overall = s;
     warm_ok = true;
