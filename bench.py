@@ -279,6 +279,118 @@ def nominal_flops_per_problem(n: int, m: int, nev: int, nprob: int) -> float:
             + 20.0 * n * n * nev + (4.0 / 3.0) * n ** 3 / max(nprob, 1))
 
 
+# ----------------------------------------------------------------------------- rooflines
+def _profile_traffic(name):
+    """Per-launch DRAM traffic from a committed ncu summary (profiles/<name>.json), or None."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", name + ".json"))).get("traffic_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def _timed_class(gevp, cls, fn, reps):
+    """Run fn() reps times with the live kernel timing on; that class's record."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    gevp.kernel_timing(True)
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    gevp.kernel_timing(False)
+    return gevp.kernel_timing_read()[cls]
+
+
+def roofline_entries(gevp, dev, live, ms_total, steps, sm_mhz):
+    """Achieved fraction of the roofline for each product kernel of the step.
+
+    live: per class, all launches of the timed region (CUDA events on the launching stream;
+    the next problem's reduction runs concurrently on a side stream, so these include
+    contention). isolated: one launch shape timed alone, the shape of the committed ncu
+    capture whose DRAM traffic is quoted: the emulated product on the reduction's shape (the
+    largest share of its time), the Gram kernel on the bench's Gram matrix, the FP64 GEMM on
+    an FP64 filter step (its largest single shape; in the default step it runs the n m^2
+    and m^3 products of the projections, CholQR and the small eigensolver).
+    Peaks: FP64 from the unit count (152 SMs x 2 FMA/clk x 2 flop x the max SM clock); BF16
+    the measured burst (isolated) and sustained (live) rates."""
+    import torch
+    mp = measured_peaks()
+    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    bf16_burst = mp.get("bf16_tflops") or 1900.0
+    bf16_sust = mp.get("bf16_tflops_sustained") or 1700.0
+    per = {}
+
+    def live_entry(cls, bound, flop_key, peak, peak_source, work):
+        rec = live[cls]
+        if rec["launches"] == 0:
+            return None
+        ach = rec[flop_key] / (max(rec["ms"], 1e-9) * 1e-3) / 1e12
+        return {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": peak_source, "work": work, "launches_per_step": rec["launches"] / max(1, steps),
+                "ms_per_launch": rec["ms"] / rec["launches"], "share_of_step": rec["ms"] / max(1e-9, ms_total),
+                "traffic": None, "traffic_note": "launch shapes vary within the step: see isolated"}
+
+    per["oz_gemm_kernel"] = live_entry(
+        "oz_gemm_kernel", "tensor", "exec_flop", bf16_sust, "BF16 sustained, of measured (MEASURED_PEAKS.json)",
+        "executed BF16 flop of the digit-pair products (36 x the FP64-equivalent 8 flop per complex "
+        "multiply-add over the K ranges processed)")
+    per["zgemm_kernel"] = live_entry(
+        "zgemm_kernel", "alu", "alg_flop", fp64_peak, "FP64 unit count x measured max SM clock",
+        "8 flop per complex multiply-add over the K ranges processed (64-block granularity)")
+    per["zgram_kernel"] = live_entry(
+        "zgram_kernel", "alu", "alg_flop", fp64_peak, "FP64 unit count x measured max SM clock",
+        "8 flop per complex multiply-add of the tiles formed (16 x 16 granularity; lower tiles of "
+        "Hermitian results)")
+    per = {k: v for k, v in per.items() if v is not None}
+
+    g = torch.Generator(device=dev).manual_seed(13)
+    # emulated product, reduction shape A B^H, 2048^3
+    if "oz_gemm_kernel" in per:
+        Ai = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
+        Bi = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
+        rec = _timed_class(gevp, "oz_gemm_kernel", lambda: gevp.zgemm_emulated(Ai, Bi, 8), 5)
+        ms = rec["ms"] / max(1, rec["launches"])
+        ach = rec["exec_flop"] / (rec["ms"] * 1e-3) / 1e12
+        per["oz_gemm_kernel"]["isolated"] = {
+            "shape": "A B^H, 2048 x 2048 x 2048 complex (the reduction's product shape)", "ms_per_launch": ms,
+            "achieved": ach, "peak": bf16_burst, "frac": ach / bf16_burst, "peak_source": "BF16 burst, of measured",
+            "traffic": _profile_traffic("oz_gemm_n2048"), "alg_bytes_per_launch": 3 * 16.0 * 2048 ** 2,
+            "fp64_equiv_tflops": rec["alg_flop"] / (rec["ms"] * 1e-3) / 1e12}
+        del Ai, Bi
+    # Gram kernel, the bench's Gram matrix Y^H Y (n 2048, m 140): 8 n m (m + 1) / 2 flop
+    if "zgram_kernel" in per:
+        n, m = 2048, 140
+        Y0 = torch.randn((n, m), dtype=torch.complex128, device=dev, generator=g)
+        Y0 = Y0 * torch.logspace(0, 3, m, dtype=torch.float64, device=dev)[None, :]
+        rec = _timed_class(gevp, "zgram_kernel", lambda: gevp.cholqr2(Y0.clone()), 5)
+        ms = rec["ms"] / max(1, rec["launches"])
+        ach = 8.0 * n * m * (m + 1) / 2 / (ms * 1e-3) / 1e12
+        per["zgram_kernel"]["isolated"] = {
+            "shape": "Gram matrix Y^H Y, n 2048, m 140 (lower triangle, 8 n m (m+1)/2 flop)", "ms_per_launch": ms,
+            "achieved": ach, "peak": fp64_peak, "frac": ach / fp64_peak, "traffic": _profile_traffic("zgram_n2048_m140"),
+            "alg_bytes_per_launch": 16.0 * n * m}
+        del Y0
+    # FP64 GEMM: one FP64 filter step C Y, n 2048 x m 140 (8 n^2 m flop), C read once
+    if "zgemm_kernel" in per:
+        Gm = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
+        Ci = (0.5 * (Gm + Gm.conj().T) * (25.0 / 2048 ** 0.5)).contiguous()
+        Yi = torch.randn((2048, 140), dtype=torch.complex128, device=dev, generator=g)
+        rec = _timed_class(gevp, "zgemm_kernel",
+                           lambda: gevp.chebyshev_filter(Ci, Yi, 4, 5.0, 80.0, -3.0, prec="fp64"), 2)
+        ms = rec["ms"] / max(1, rec["launches"])
+        ach = rec["alg_flop"] / (rec["ms"] * 1e-3) / 1e12
+        per["zgemm_kernel"]["isolated"] = {
+            "shape": "FP64 filter step C.Y, n 2048 x m 140", "ms_per_launch": ms, "achieved": ach,
+            "peak": fp64_peak, "frac": ach / fp64_peak, "traffic": _profile_traffic("zgemm_filter_n2048_m140"),
+            "alg_bytes_per_launch": 16.0 * 2048 ** 2 + 48.0 * 2048 * 140}
+        del Gm, Ci, Yi
+    top = max(per, key=lambda k: per[k]["share_of_step"])
+    out = dict(per[top])
+    out["kernel"] = top
+    out["per_kernel"] = per
+    return out
+
+
 # ----------------------------------------------------------------------------- CPU oracle baseline
 def cpu_baseline(seq, n_solves_budget_s: float, flops_per_problem: float):
     """Time the FP64 CPU oracle (tridiagonal path, all host cores) on a bounded sample of the
@@ -564,92 +676,10 @@ def main():
     value = world * nominal / (ms_step * 1e-3) / 1e12
     executed_tflops = world * flops / (ms_step * 1e-3) / 1e12
 
-    # ---- roofline of the dominant kernel, from the live timing of the timed region: the
-    # GEMM class with the larger device time (the emulated product when the reduction and
-    # the n^2 m products are emulated, else the FP64 complex GEMM)
+    # ---- per-kernel rooflines, from the live timing of the timed region; the top-level
+    # entry is the kernel class with the largest device time
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
-    # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock x 2 flop
-    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    mp = measured_peaks()
-    oz, zg = live["oz_gemm_kernel"], live["zgemm_kernel"]
-    if oz["ms"] >= zg["ms"] and oz["launches"] > 0:
-        ms_launch = oz["ms"] / oz["launches"]
-        achieved = oz["exec_flop"] / (oz["ms"] * 1e-3) / 1e12
-        peak = mp.get("bf16_tflops_sustained") or 1700.0
-        roofline = {"bound": "tensor", "kernel": "oz_gemm_kernel (emulated FP64 complex product, 8 digits)",
-                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "peak_source": "BF16 sustained, of measured (MEASURED_PEAKS.json)",
-                    "work": "executed BF16 flop of the digit-pair products (36 x the FP64-equivalent 8 flop per "
-                            "complex multiply-add over the K ranges processed)",
-                    "launches_per_step": oz["launches"] / max(1, args.steps), "ms_per_launch": ms_launch,
-                    "fp64_equiv_tflops": oz["alg_flop"] / (oz["ms"] * 1e-3) / 1e12,
-                    "share_of_step": oz["ms"] / max(1e-9, ms_total), "zgemm_share_of_step": zg["ms"] / max(1e-9, ms_total),
-                    "traffic_note": "launch shapes vary within the step: traffic is given for the isolated launch"}
-        # isolated reference launch with the shape of the committed ncu capture (A B^H, n 2048)
-        g = torch.Generator(device=dev).manual_seed(13)
-        Ai = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
-        Bi = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
-        for _ in range(2):
-            gevp.zgemm_emulated(Ai, Bi, 8)
-        torch.cuda.synchronize()
-        gevp.kernel_timing(True)
-        for _ in range(5):
-            gevp.zgemm_emulated(Ai, Bi, 8)
-        torch.cuda.synchronize()
-        gevp.kernel_timing(False)
-        iso = gevp.kernel_timing_read()["oz_gemm_kernel"]
-        iso_ms = iso["ms"] / max(1, iso["launches"])
-        iso_ach = iso["exec_flop"] / (iso["ms"] * 1e-3) / 1e12
-        traffic = None
-        prof = os.path.join(ROOT, "profiles", "oz_gemm_n2048.json")
-        if os.path.exists(prof):
-            try:
-                traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
-            except (OSError, ValueError):
-                traffic = None
-        burst = mp.get("bf16_tflops") or 1900.0
-        roofline["isolated"] = {"shape": "A B^H, 2048 x 2048 x 2048 complex", "ms_per_launch": iso_ms,
-                                "achieved": iso_ach, "peak": burst, "frac": iso_ach / burst, "traffic": traffic,
-                                "fp64_equiv_tflops": iso["alg_flop"] / (iso["ms"] * 1e-3) / 1e12}
-        del Ai, Bi
-    else:
-        ms_launch = zg["ms"] / max(1, zg["launches"])
-        achieved = zg["alg_flop"] / (max(zg["ms"], 1e-9) * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": "zgemm_kernel (FP64 complex GEMM, all launches of the step)",
-                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                    "traffic": None,
-                    "peak_source": "FP64 unit count x measured max SM clock (152 SM x 2 FMA/clk x 2 flop)",
-                    "work": "8 flop per complex multiply-add over the K ranges processed (64-block granularity)",
-                    "launches_per_step": zg["launches"] / max(1, args.steps), "ms_per_launch": ms_launch,
-                    "share_of_step": zg["ms"] / max(1e-9, ms_total),
-                    "oz_share_of_step": oz["ms"] / max(1e-9, ms_total),
-                    "traffic_note": "launch shapes vary within the step: traffic is given for the isolated launch"}
-        # isolated reference launch with the shape of the committed ncu capture: one FP64
-        # Chebyshev filter step C.Y, n 2048 x m 140 (8 n^2 m flop), C read once per launch
-        g = torch.Generator(device=dev).manual_seed(7)
-        Gm = torch.randn((2048, 2048), dtype=torch.complex128, device=dev, generator=g)
-        Ci = (0.5 * (Gm + Gm.conj().T) * (25.0 / 2048 ** 0.5)).contiguous()
-        Yi = torch.randn((2048, 140), dtype=torch.complex128, device=dev, generator=g)
-        gevp.chebyshev_filter(Ci, Yi, 2, 5.0, 80.0, -3.0, prec="fp64")
-        torch.cuda.synchronize()
-        gevp.kernel_timing(True)
-        gevp.chebyshev_filter(Ci, Yi, 16, 5.0, 80.0, -3.0, prec="fp64")
-        torch.cuda.synchronize()
-        gevp.kernel_timing(False)
-        iso = gevp.kernel_timing_read()["zgemm_kernel"]
-        iso_ms = iso["ms"] / max(1, iso["launches"])
-        iso_ach = iso["alg_flop"] / (iso["ms"] * 1e-3) / 1e12
-        traffic = None
-        prof = os.path.join(ROOT, "profiles", "zgemm_filter_n2048_m140.json")
-        if os.path.exists(prof):
-            try:
-                traffic = json.load(open(prof)).get("traffic_bytes_per_launch")
-            except (OSError, ValueError):
-                traffic = None
-        roofline["isolated"] = {"shape": "FP64 filter step C.Y, n 2048 x m 140", "ms_per_launch": iso_ms,
-                                "achieved": iso_ach, "peak": fp64_peak, "frac": iso_ach / fp64_peak,
-                                "traffic": traffic, "alg_bytes_per_launch": 16.0 * 2048 ** 2 + 48.0 * 2048 * 140}
-        del Gm, Ci, Yi
+    roofline = roofline_entries(gevp, dev, live, ms_total, args.steps, sm_mhz)
 
     # ---- plain FP64 cold-start GPU solver on the same sequence (the comparison form)
     compare = None

@@ -16,6 +16,7 @@
 #include "../../include/gevp.h"
 
 #include <algorithm>
+#include <initializer_list>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -300,13 +301,21 @@ gevp_status sync_read(gevp_ctx* h, const void* dsrc, void* hdst, size_t bytes) {
   return GEVP_OK;
 }
 
-// two device-to-host reads with one synchronisation
-gevp_status sync_read2(gevp_ctx* h, const void* d1, void* h1, size_t b1, const void* d2, void* h2, size_t b2) {
-  CK(cudaMemcpyAsync(h1, d1, b1, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h2, d2, b2, cudaMemcpyDeviceToHost, h->stream));
+// several device-to-host reads with one synchronisation
+struct ReadSpec {
+  const void* dev;
+  void* host;
+  size_t bytes;
+};
+gevp_status sync_reads(gevp_ctx* h, std::initializer_list<ReadSpec> reads) {
+  for (const ReadSpec& r : reads)
+    if (r.bytes) CK(cudaMemcpyAsync(r.host, r.dev, r.bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return GEVP_OK;
+}
+gevp_status sync_read2(gevp_ctx* h, const void* d1, void* h1, size_t b1, const void* d2, void* h2, size_t b2) {
+  return sync_reads(h, {{d1, h1, b1}, {d2, h2, b2}});
 }
 
 // ---------------------------------------------------------------- building blocks
@@ -529,10 +538,15 @@ bool cholqr_pass(gevp_ctx* h, int64_t n, int ma, const double2* src, int64_t lds
 // accepted only after two consecutive plain passes (so a shifted pass is always followed
 // by CholQR2). A block that stays rank deficient is replaced by fresh random columns
 // (projected against the locked ones).
+// pending (nullable): the two-pass fast path is only enqueued and *pending set to 1; the
+// caller reads the passes' statuses h->info[0..1] later (with its next read) and, if either
+// is set, calls again with allow_fast = false (Y is left intact by the fast path).
 gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_t ldy, int ma, double2* Out,
-                           int64_t ldo, gevp_stats* st, uint64_t seed = 0) {
+                           int64_t ldo, gevp_stats* st, uint64_t seed = 0, int* pending = nullptr,
+                           bool allow_fast = true) {
   const int64_t ldq = h->cap_m;
   const bool fast = ma <= cholinv_max_order();
+  if (pending) *pending = 0;
   for (int restart = 0; restart < 2; ++restart) {
     for (int pass = 0; pass < 2 && nlock > 0; ++pass) {
       zgram(n, nlock, ma, h->Q, ldq, Y, ldy, h->P, ma, 0, h->split, h->split_elems, h->gcnt, h->stream);
@@ -540,13 +554,17 @@ gevp_status orthonormalize(gevp_ctx* h, int64_t n, int nlock, double2* Y, int64_
       u.Cin = Y; u.ldc = ldy; u.beta = 1.0;
       zgemm(u, h->split, h->split_elems, h->stream);
     }
-    if (fast && restart == 0) {
+    if (fast && allow_fast && restart == 0) {
       CK(cudaMemsetAsync(h->info, 0, 2 * sizeof(int), h->stream));
       if (cholqr_pass(h, n, ma, Y, ldy, h->Xf, ldq, 0.0, h->info) &&
           cholqr_pass(h, n, ma, h->Xf, ldq, Out, ldo, 0.0, h->info + 1)) {
+        if (st) st->flops_fp64 += 2 * 8.0 * (double)n * ma * ma;
+        if (pending) {
+          *pending = 1;
+          return GEVP_OK;
+        }
         int inf[2] = {0, 0};
         TRY(sync_read(h, h->info, inf, sizeof inf));
-        if (st) st->flops_fp64 += 2 * 8.0 * (double)n * ma * ma;
         if (inf[0] == 0 && inf[1] == 0) return GEVP_OK;
       }
     }
@@ -634,13 +652,14 @@ gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const doubl
   // G = Q^H C Q is Hermitian: its lower tiles only, both triangles written
   zgram(n, ma, ma, Qa, ld, h->Wt, ld, h->G, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
   heev_small(ma, h->G, ma, h->theta + nlock, h->Zs, ma, h->hw, refine, h->stream);
-  // [Q W] <- [Q Wt] Z in one launch (a batch of two products sharing Z; Q's goes through Y1)
-  ZgemmArgs q = zg((int)n, ma, ma, Qa, ld, 0, h->Zs, ma, 0, h->Y1, ld);
+  // [Q W] <- [Q Wt] Z in one launch (a batch of two products sharing Z; Q's goes through
+  // Xf, free until the final check, so that the filtered block in Y1/Y2 stays intact)
+  ZgemmArgs q = zg((int)n, ma, ma, Qa, ld, 0, h->Zs, ma, 0, h->Xf, ld);
   q.batch = 2;
   q.sA = h->Wt - Qa;
-  q.sD = (h->W + nlock) - h->Y1;
+  q.sD = (h->W + nlock) - h->Xf;
   zgemm(q, h->split, h->split_elems, h->stream);
-  zcopy2d(n, ma, h->Y1, ld, Qa, ld, h->stream);
+  zcopy2d(n, ma, h->Xf, ld, Qa, ld, h->stream);
   resid_norms(n, ma, h->W + nlock, ld, Qa, ld, h->theta + nlock, h->res + nlock, h->partial, h->stream);
   if (st) st->flops_fp64 += 8.0 * ((double)n * n * ma + 3.0 * n * ma * ma) + 32.0 * refine * (double)ma * ma * ma;
   return GEVP_OK;
@@ -896,11 +915,25 @@ gevp_status solve_one(gevp_ctx* h, int64_t n, const double2* A, int64_t lda, con
       st->matvecs += (int64_t)deg * ma;
     }
     tm.mark(PH_FILTER);
-    TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st, o.seed + 31ull * it + 7ull * prob_index));
+    const uint64_t oseed = o.seed + 31ull * it + 7ull * prob_index;
+    int pend = 0;
+    TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st, oseed, &pend));
     tm.mark(PH_ORTH);
     TRY(rayleigh_ritz(h, n, S.nlock, ma, h->C, n, o.refine_iters, st));
-    TRY(sync_read2(h, h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double), h->res + S.nlock,
-                   S.res.data() + S.nlock, ma * sizeof(double)));
+    // one status read per round: the Ritz values, residuals and the CholQR passes' pivots
+    int orth_info[2] = {0, 0};
+    TRY(sync_reads(h, {{h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double)},
+                       {h->res + S.nlock, S.res.data() + S.nlock, ma * sizeof(double)},
+                       {h->info, orth_info, pend ? sizeof orth_info : 0}}));
+    if (pend && (orth_info[0] != 0 || orth_info[1] != 0)) {
+      // a CholQR pass met a non-positive pivot: the projection above used a bad basis.
+      // Orthonormalise the (intact) filtered block again with the shifted fallback and
+      // project again
+      TRY(orthonormalize(h, n, S.nlock, Yf, ld, ma, h->Q + S.nlock, ld, st, oseed, nullptr, false));
+      TRY(rayleigh_ritz(h, n, S.nlock, ma, h->C, n, o.refine_iters, st));
+      TRY(sync_read2(h, h->theta + S.nlock, S.theta.data() + S.nlock, ma * sizeof(double), h->res + S.nlock,
+                     S.res.data() + S.nlock, ma * sizeof(double)));
+    }
     tm.mark(PH_RR);
     S.have_theta = true;
     if (st) st->outer_iters++;

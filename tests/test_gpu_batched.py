@@ -137,17 +137,25 @@ def test_batched_errors(cuda):
 
 @pytest.mark.slow
 def test_full_size_kpoint_batch(cuda, orc):
-    """64 k-points, n ~ U{800..3000}, nev = round(0.06 n), two warm steps, FP32-class filter:
-    every residual <= tol; the oracle's eigenvalues on the two smallest k-points."""
+    """The batching form as specified: 64 k-points, n ~ U{800..3000}, nev = round(0.06 n),
+    a ten-step warm-started sequence per k-point, all solved by one batched call with the
+    FP32-class filter. Every residual <= tol; step 0 of every k-point against its
+    closed-form spectrum; the oracle's eigenvalues at the last step on four k-points spread
+    over the lower half of the size range (an oracle solve of the largest orders takes
+    minutes on the host); the rounds ran as replays of the captured round graph."""
     from paper_1007_4400_gb300 import synth
     sizes = synth.batched_sizes(64)
-    seqs = synth.kpoint_batch(64, 2, device=cuda, sizes=sizes)
+    seqs = synth.kpoint_batch(64, 10, device=cuda, sizes=sizes)
     r = _solve(seqs, "fp32", want_X=False)
     assert r.status == 0, r.stats
+    assert r.stats["steps"] == 10 and r.stats["graph_replays"] > 0
     for k in range(64):
-        assert r.resid[k].max().item() <= TOL_RES
-    order = np.argsort([n for n, _, _ in sizes])[:2]
-    for k in order:
         s = seqs[k]
-        lam_r, _ = orc.solve(s.A[1].cpu().numpy(), s.B.cpu().numpy(), s.nev, method="tridiag")
-        assert np.abs(r.Lambda[k][1].cpu().numpy() - lam_r).max() <= TOL_LAM * np.abs(lam_r).max()
+        assert r.resid[k].max().item() <= TOL_RES
+        lam0 = r.Lambda[k][0].cpu().numpy()
+        assert np.abs(lam0 - s.lam0[:s.nev]).max() <= TOL_LAM * np.abs(s.lam0).max(), (k, s.n)
+    order = np.argsort([n for n, _, _ in sizes])
+    for k in order[[0, 8, 16, 32]]:
+        s = seqs[k]
+        lam_r, _ = orc.solve(s.A[-1].cpu().numpy(), s.B.cpu().numpy(), s.nev, method="tridiag")
+        assert np.abs(r.Lambda[k][-1].cpu().numpy() - lam_r).max() <= TOL_LAM * np.abs(lam_r).max(), (k, s.n)

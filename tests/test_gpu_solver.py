@@ -196,3 +196,32 @@ def test_refresh_policy(cuda, orc, eps0, decay):
     for l in (1, 5):
         _check_problem(orc, s.A[l].cpu().numpy(), B, r.Lambda[l].cpu().numpy(), r.X[l].cpu().numpy(),
                        r.resid[l].cpu().numpy(), nev, method="jacobi")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cholqr_breakdown_inside_the_rounds(cuda, orc, prec):
+    """A spectrum with one cluster of wanted values far below a single, highly degenerate
+    unwanted value: the filter drives the whole block towards the 4-dimensional wanted
+    space, the Gram matrix of the filtered block is numerically singular, and the plain
+    CholQR pass inside a round fails. The solver must notice it (the status of the pass is
+    read with the round's Ritz values), repeat the orthonormalisation with the shifted
+    fallback, and still return the oracle's eigenpairs."""
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(881)
+    n, nev, nex = 64, 4, 4
+    lam = np.concatenate([[-2.0, -1.9, -1.8, -1.7], np.full(n - 4, 50.0)])
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    Q = Q * (np.diag(R) / np.abs(np.diag(R)))
+    L = np.tril(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), -1) * (0.3 / np.sqrt(n))
+    L = L + np.diag(rng.uniform(0.5, 2.0, n))
+    B = L @ L.conj().T
+    B = 0.5 * (B + B.conj().T)
+    A = L @ (Q * lam) @ Q.conj().T @ L.conj().T
+    A = 0.5 * (A + A.conj().T)
+    r = gevp.solve_sequence([torch.from_numpy(A).to(cuda)], torch.from_numpy(B).to(cuda), nev, nex=nex,
+                            cold_start=1, filter_prec=prec, deg_min=24)
+    assert r.status == 0, r.stats
+    assert r.stats[0]["orth_fallbacks"] > 0
+    _check_problem(orc, A, B, r.Lambda[0].cpu().numpy(), r.X.cpu().numpy(), r.resid[0].cpu().numpy(), nev,
+                   method="jacobi", lam_true=lam)
