@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--seq-steps", type=int, default=10, help="kpoint_batch workload: problems per k-point")
     p.add_argument("--reduce-slices", type=int, default=8,
                    help="digits of the emulated FP64 products of the reduction (0: FP64 pipe)")
-    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki", "seq_small", "cholqr"],
+    p.add_argument("--kernel-case", choices=["zgemm", "tc", "reduce", "batched", "variation", "ozaki", "seq_small", "cholqr",
+                            "update"],
                    default=None,
                    help="run only a few launches of one kernel (n 2048, m 140) for ncu captures")
     return p.parse_args()
@@ -91,6 +92,45 @@ def kernel_case(args):
         r = gevp.solve_sequence([a.to(dev) for a in seq.A], seq.B.to(dev), 64, nex=24, filter_prec="fp32")
         torch.cuda.synchronize()
         print(f"kernel case seq_small done: status {r.status}, max residual {float(r.resid.max()):.2e}")
+        return 0
+    if args.kernel_case == "update":
+        # the localised update of the standard form (64 of 2048 rows and columns changed,
+        # 8 digits) against a full emulated reduction, timed with CUDA events; the factor of
+        # B is reused by the update and part of the full reduction's call, so the factor-only
+        # time (an update of one row with a fresh factorisation) is measured and subtracted
+        import numpy as np
+        n, k = 2048, 64
+        seq = synth.make_sequence(1, n, 1, 100, 40, device=dev)
+        rng = np.random.default_rng(7)
+        J = np.sort(rng.choice(n, size=k, replace=False))
+        D = torch.randn((n, n), dtype=torch.complex128, device=dev)
+        D = 0.5 * (D + D.conj().T)
+        mask = torch.zeros((n, n), dtype=torch.bool, device=dev)
+        mask[torch.from_numpy(J).to(dev), :] = True
+        mask[:, torch.from_numpy(J).to(dev)] = True
+        dA = torch.where(mask, D, torch.zeros_like(D)) * 0.01
+        _, C0 = gevp.reduce(seq.A[0], seq.B, slices=8)
+
+        def timed(f, reps=5):
+            for _ in range(2):
+                f()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+        ms_full = timed(lambda: gevp.reduce(seq.A[0], seq.B, slices=8))
+        ms_factor = timed(lambda: gevp.reduce_update(C0.clone(), seq.B, dA, J[:1], slices=8))
+        gevp.reduce_update(C0.clone(), seq.B, dA, J, slices=8)
+        ms_upd = timed(lambda: gevp.reduce_update(C0.clone(), seq.B, dA, J, slices=8, reuse_factor=True))
+        ms_upd64 = timed(lambda: gevp.reduce_update(C0.clone(), seq.B, dA, J, slices=0, reuse_factor=True))
+        ms_copy = timed(lambda: C0.clone())
+        print(json.dumps({"kernel_case": "update", "n": n, "k": k, "ms_full_reduction_with_factor": ms_full,
+                          "ms_factor_only": ms_factor, "ms_full_reduction_products": ms_full - ms_factor,
+                          "ms_update_emulated": ms_upd - ms_copy, "ms_update_fp64": ms_upd64 - ms_copy}))
         return 0
     if args.kernel_case == "cholqr":
         # the bench shape of the tall-skinny kernels: CholQR2 of a 2048 x 140 block with

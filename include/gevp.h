@@ -124,6 +124,30 @@ const char* gevp_version(void);
 gevp_status gevp_reduce(gevp_handle h, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
                         void* L, int64_t ldl, void* C, int64_t ldc, int64_t* info);
 
+/* Update of the standard form for a change of A confined to a few rows and columns. The
+ * paper observes that most entries of the Hamiltonian change little from one iteration to
+ * the next, so that only part of it needs to be regenerated (Sec. "Matrix generation").
+ * With B (hence L) unchanged, C_new = L^-1 A_new L^-H = C_old + L^-1 dA L^-H, and when
+ * dA = A_new - A_old vanishes outside the rows and the columns of an index set J (|J| = k),
+ * the update is the Hermitian rank-2k product U V^H + V U^H with U = L^-1 E_J (the columns J
+ * of L^-1), R = the rows J of dA and V = L^-1 R^H - U R_JJ / 2: O(n^2 k) work instead of the
+ * 4 n^3 of a full reduction. The result equals the full reduction of A_new up to rounding.
+ *   B: n x n HPD (ld ldb). reuse_factor 1: B is the matrix of the previous successful call
+ *   on this handle (same pointer and contents) and its factorisation is reused; 0: B is
+ *   factored (and kept for the next call).
+ *   dA: n x n Hermitian difference (ld ldda), read only in the rows and columns listed; its
+ *   other entries are ignored (treated as zero). rows: host array of k distinct indices in
+ *   [0, n), 0 <= k <= n / 5 (beyond that a full reduction costs about as much).
+ *   C: n x n (ld ldc) in: C_old = L^-1 A_old L^-H (Hermitian, both triangles); out: C_new,
+ *   Hermitian (both triangles written).
+ *   slices: 0 = FP64 pipe; 1..8 = the two n^2 k products emulated on the tensor cores as in
+ *   gevp_zgemm_emulated (requires n <= 30720).
+ *   *info (host): 0, or the potrf pivot of B (then GEVP_ERR_NOT_HPD). GEVP_ERR_INVALID_ARG
+ *   for repeated or out-of-range rows or k > n / 5. Returns after the work is complete. */
+gevp_status gevp_reduce_update(gevp_handle h, int64_t n, const void* B, int64_t ldb, int reuse_factor,
+                               const void* dA, int64_t ldda, int k, const int64_t* rows, void* C, int64_t ldc,
+                               int slices, int64_t* info);
+
 /* The sequence solver (the paper's sequence {P_i} of correlated problems, each seeded
  * with the eigenvectors of the one before).
  *   A: host array of nprob device pointers, each n x n (ld lda). B: host array of nprob

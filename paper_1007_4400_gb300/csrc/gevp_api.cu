@@ -70,6 +70,13 @@ struct gevp_ctx {
   // solver products on the main stream: C (rows, per problem), A (rows, per final check),
   // B (rows, kept while the factorisation is), the block (columns, per product)
   gevp::OzOperand ozC, ozA, ozB, ozQ, ozLH;
+  gevp::OzOperand ozQW, ozZ;                // the Rayleigh-Ritz rotation [Q; W] Z (rows, columns)
+  gevp::OzOperand ozR, ozUV, ozVU;          // the localised update of the standard form
+  // localised update: the B whose factorisation the last update call left (and its n, gen)
+  const void* upd_B = nullptr;
+  int64_t upd_n = 0, upd_gen = -1;
+  int64_t* jidx = nullptr;                  // device copy of the changed rows
+  size_t jidx_cap = 0;
   int64_t ozLH_gen = -1;                    // chol_gen the L^-H rows (ozLH) were split from
   double* ozws = nullptr;                   // split-K partials of the thin emulated products
   size_t ozws_doubles = 0;
@@ -652,14 +659,33 @@ gevp_status rayleigh_ritz(gevp_ctx* h, int64_t n, int nlock, int ma, const doubl
   // G = Q^H C Q is Hermitian: its lower tiles only, both triangles written
   zgram(n, ma, ma, Qa, ld, h->Wt, ld, h->G, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
   heev_small(ma, h->G, ma, h->theta + nlock, h->Zs, ma, h->hw, refine, h->stream);
-  // [Q W] <- [Q Wt] Z in one launch (a batch of two products sharing Z; Q's goes through
-  // Xf, free until the final check, so that the filtered block in Y1/Y2 stays intact)
-  ZgemmArgs q = zg((int)n, ma, ma, Qa, ld, 0, h->Zs, ma, 0, h->Xf, ld);
-  q.batch = 2;
-  q.sA = h->Wt - Qa;
-  q.sD = (h->W + nlock) - h->Xf;
-  zgemm(q, h->split, h->split_elems, h->stream);
-  zcopy2d(n, ma, h->Xf, ld, Qa, ld, h->stream);
+  // [Q W] <- [Q Wt] Z. Emulated (when C's products are): the two blocks stacked into the
+  // free n x n scratch T as one 2n x ma operand, so that one product fills the SMs; else one
+  // FP64 launch (a batch of two products sharing Z). Q's result goes through T or Xf (free
+  // until the final check), so that the filtered block in Y1/Y2 stays intact.
+  const int S = h->oz_slices;
+  const size_t qw_bytes = S > 0 ? gevp::oz_operand_bytes(2 * (int)n, ma, S, 2) + gevp::oz_operand_bytes(ma, ma, S, 3)
+                                : 0;
+  // (the emulated operands' memory is reserved for this n while C's digits are held)
+  if (S > 0 && h->ozC_src == (const void*)C && 2 * n * (int64_t)ma <= n * n &&
+      qw_bytes <= gevp::oz_operand_bytes((int)n, (int)n, S, 3)) {
+    zcopy2d(n, ma, Qa, ld, h->T, ma, h->stream);
+    zcopy2d(n, ma, h->Wt, ld, h->T + n * ma, ma, h->stream);
+    char* mem = oz_region(h, n, 2);
+    CK(gevp::oz_split(h->ozQW, mem, 2 * (int)n, ma, h->T, ma, 0, 0, S, 2, h->ozflags + 1, h->stream));
+    CK(gevp::oz_split(h->ozZ, mem + gevp::oz_operand_bytes(2 * (int)n, ma, S, 2), ma, ma, h->Zs, ma, 0, 0, S, 3,
+                      h->ozflags + 1, h->stream, true));
+    CK(gevp::oz_gemm(h->ozQW, h->ozZ, 0, 0, h->T, ma, h->ozflags, h->stream, nullptr, h->ozws, h->ozws_doubles));
+    zcopy2d(n, ma, h->T, ma, Qa, ld, h->stream);
+    zcopy2d(n, ma, h->T + n * ma, ma, h->W + nlock, ld, h->stream);
+  } else {
+    ZgemmArgs q = zg((int)n, ma, ma, Qa, ld, 0, h->Zs, ma, 0, h->Xf, ld);
+    q.batch = 2;
+    q.sA = h->Wt - Qa;
+    q.sD = (h->W + nlock) - h->Xf;
+    zgemm(q, h->split, h->split_elems, h->stream);
+    zcopy2d(n, ma, h->Xf, ld, Qa, ld, h->stream);
+  }
   resid_norms(n, ma, h->W + nlock, ld, Qa, ld, h->theta + nlock, h->res + nlock, h->partial, h->stream);
   if (st) st->flops_fp64 += 8.0 * ((double)n * n * ma + 3.0 * n * ma * ma) + 32.0 * refine * (double)ma * ma * ma;
   return GEVP_OK;
@@ -1109,6 +1135,7 @@ gevp_status gevp_destroy(gevp_handle h) {
     if (h->ozmem[i]) cudaFree(h->ozmem[i]);
   if (h->ozflags) cudaFree(h->ozflags);
   if (h->ozws) cudaFree(h->ozws);
+  if (h->jidx) cudaFree(h->jidx);
   if (h->hb2) cudaFreeHost(h->hb2);
   for (cudaEvent_t e : {h->ev_main, h->ev_side, h->ev_user})
     if (e) cudaEventDestroy(e);
@@ -1144,6 +1171,130 @@ gevp_status gevp_reduce(gevp_handle h, int64_t n, const void* A, int64_t lda, co
   h->chol_valid = false;   // the caller's next solve refactors
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
+  return GEVP_OK;
+}
+
+gevp_status gevp_reduce_update(gevp_handle h, int64_t n, const void* B, int64_t ldb, int reuse_factor,
+                               const void* dA, int64_t ldda, int k, const int64_t* rows, void* C, int64_t ldc,
+                               int slices, int64_t* info) {
+  if (!h || n < 0 || k < 0 || !info || slices < 0 || slices > gevp::kOzSlicesMax) return GEVP_ERR_INVALID_ARG;
+  *info = 0;
+  if (n == 0) return GEVP_OK;
+  if (!B || !C || bad_ld(ldb, n) || bad_ld(ldc, n)) return GEVP_ERR_INVALID_ARG;
+  if (k > 0 && (!dA || !rows || bad_ld(ldda, n))) return GEVP_ERR_INVALID_ARG;
+  if ((int64_t)5 * k > n) return GEVP_ERR_INVALID_ARG;
+  {
+    std::vector<char> seen((size_t)n, 0);
+    for (int t = 0; t < k; ++t) {
+      if (rows[t] < 0 || rows[t] >= n || seen[(size_t)rows[t]]) return GEVP_ERR_INVALID_ARG;
+      seen[(size_t)rows[t]] = 1;
+    }
+  }
+  if (k == 0) return GEVP_OK;
+  if (slices > 0 && n > 30720) {
+    h->err = "emulated product: n above 30720";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  cudaSetDevice(h->device);
+  if (slices > 0 && !gevp::oz_supported()) {
+    h->err = "emulated FP64 products need an sm_103 device";
+    return GEVP_ERR_UNSUPPORTED;
+  }
+  TRY(ensure(h, n, k));
+  if (!(reuse_factor && h->chol_valid && h->upd_B == B && h->upd_n == n && h->upd_gen == h->chol_gen)) {
+    h->upd_B = nullptr;
+    TRY(factor_B(h, n, (const double2*)B, ldb, info));
+    h->upd_B = B;
+    h->upd_n = n;
+    h->upd_gen = h->chol_gen;
+  }
+  if ((size_t)k > h->jidx_cap) {
+    if (h->jidx) {
+      cudaStreamSynchronize(h->stream);
+      cudaFree(h->jidx);
+    }
+    h->jidx = nullptr;
+    h->jidx_cap = 0;
+    void* p = nullptr;
+    CK(cudaMalloc(&p, (size_t)k * sizeof(int64_t)));
+    h->jidx = (int64_t*)p;
+    h->jidx_cap = (size_t)k;
+  }
+  CK(cudaMemcpyAsync(h->jidx, rows, (size_t)k * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));   // rows is pageable host memory of the caller
+  // scratch in T (n x n): UV = [U V] and VU = [V U] (n x 2k each), R = rows J of dA (k x n);
+  // R_JJ (k x k) in G
+  const int64_t k2 = 2 * (int64_t)k;
+  double2* UV = h->T;
+  double2* VU = h->T + n * k2;
+  double2* R = h->T + 2 * n * k2;
+  double2* RJJ = h->G;
+  cudaStream_t s = h->stream;
+  gather_cols(n, k, h->Linv, n, h->jidx, UV, k2, s);                       // U = L^-1 E_J
+  gather_rows(k, n, (const double2*)dA, ldda, h->jidx, R, n, s);          // R = E_J^T dA
+  gather_cols(k, k, R, n, h->jidx, RJJ, k, s);                             // R_JJ
+  const int keep = h->oz_slices;
+  h->oz_slices = slices;
+  gevp_status st = GEVP_OK;
+  if (slices > 0) {
+    // W = L^-1 R^H (L^-1 rows, lower; columns of R^H = conjugated rows of R), emulated
+    const int S = slices;
+    const int nn = (int)n;
+    const size_t bA = gevp::oz_operand_bytes(nn, nn, S, 2);
+    st = oz_reserve(h, 0, oz_main_bytes(n, S));
+    if (st == GEVP_OK && (h->oz_l_gen != h->chol_gen || h->oz_l_S != S)) {
+      char* mem = h->ozmem[0];
+      if (gevp::oz_split(h->ozLA, mem, nn, nn, h->Linv, n, 0, 2, S, 2, h->ozflags + 1, s) != cudaSuccess ||
+          gevp::oz_split(h->ozLB, mem + bA, nn, nn, h->Linv, n, 1, 2, S, 3, h->ozflags + 1, s) != cudaSuccess)
+        st = cuda_fail(h, cudaGetLastError(), "oz_split");
+      h->oz_l_gen = h->chol_gen;
+      h->oz_l_S = S;
+    }
+    if (st == GEVP_OK &&
+        (gevp::oz_split(h->ozR, oz_region(h, n, 2), k, nn, R, n, 1, 0, S, 3, h->ozflags + 1, s) != cudaSuccess ||
+         gevp::oz_gemm(h->ozLA, h->ozR, 1, 0, UV + k, k2, h->ozflags, s, nullptr, h->ozws, h->ozws_doubles) !=
+             cudaSuccess))
+      st = cuda_fail(h, cudaGetLastError(), "oz_gemm");
+  } else {
+    ZgemmArgs w = zg((int)n, k, (int)n, h->Linv, n, 0, R, n, 1, UV + k, k2);
+    w.triA = 1;
+    zgemm(w, h->split, h->split_elems, s);
+  }
+  if (st == GEVP_OK) {
+    // V = W - U R_JJ / 2 (in place over W)
+    ZgemmArgs v = zg((int)n, k, k, UV, k2, 0, RJJ, k, 0, UV + k, k2, -0.5);
+    v.Cin = UV + k; v.ldc = k2; v.beta = 1.0;
+    zgemm(v, h->split, h->split_elems, s);
+    zcopy2d(n, k, UV + k, k2, VU, k2, s);
+    zcopy2d(n, k, UV, k2, VU + k, k2, s);
+    // C += [U V] [V U]^H = U V^H + V U^H, lower triangle, then its Hermitian completion
+    if (slices > 0) {
+      const int nn = (int)n;
+      // [U V] rows in the T/C region, the conjugated rows of [V U] from the A region on
+      // (up to three regions' room: the cached digits of B and of L^-H are invalidated)
+      h->ozB_src = nullptr;
+      h->ozB_gen = -1;
+      h->ozLH_gen = -1;
+      if (gevp::oz_split(h->ozUV, oz_region(h, n, 3), nn, (int)k2, UV, k2, 0, 0, slices, 2, h->ozflags + 1, s) !=
+              cudaSuccess ||
+          gevp::oz_split(h->ozVU, oz_region(h, n, 4), nn, (int)k2, VU, k2, 1, 0, slices, 3, h->ozflags + 1, s) !=
+              cudaSuccess ||
+          gevp::oz_gemm(h->ozUV, h->ozVU, 0, 0, h->C, n, h->ozflags, s) != cudaSuccess)
+        st = cuda_fail(h, cudaGetLastError(), "oz_gemm");
+      if (st == GEVP_OK) add_lower_herm(n, (double2*)C, ldc, h->C, n, s);
+    } else {
+      ZgemmArgs u = zg((int)n, (int)n, (int)k2, UV, k2, 0, VU, k2, 1, (double2*)C, ldc);
+      u.Cin = (const double2*)C; u.ldc = ldc; u.beta = 1.0;
+      u.triD = 1;
+      zgemm(u, h->split, h->split_elems, s);
+      hermitize_lower(n, (double2*)C, ldc, s);
+    }
+  }
+  h->oz_slices = keep;
+  if (st != GEVP_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (slices > 0) TRY(oz_check(h));
   return GEVP_OK;
 }
 

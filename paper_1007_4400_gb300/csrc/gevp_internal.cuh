@@ -97,6 +97,13 @@ void hermitize_lower(int64_t n, double2* C, int64_t ldc, cudaStream_t s);   // u
 void hermitize_avg(int64_t n, double2* C, int64_t ldc, cudaStream_t s);     // C <- (C + C^H)/2
 // lower triangle scaled by sign * (*scale) (device scalar), then upper <- conj(lower)
 void hermitize_scale_lower(int64_t n, double2* C, int64_t ldc, const double* scale, double sign, cudaStream_t s);
+// C <- C + D on the lower triangle, then upper <- conj(lower), real diagonal
+void add_lower_herm(int64_t n, double2* C, int64_t ldc, const double2* D, int64_t ldd, cudaStream_t s);
+// Out[i][t] = X[i][idx[t]] (rows x k) and Out[t][j] = X[idx[t]][j] (k x cols); idx device
+void gather_cols(int64_t rows, int k, const double2* X, int64_t ldx, const int64_t* idx, double2* Out, int64_t ldo,
+                 cudaStream_t s);
+void gather_rows(int k, int64_t cols, const double2* X, int64_t ldx, const int64_t* idx, double2* Out, int64_t ldo,
+                 cudaStream_t s);
 // E[p] = sum of lam[p * nev + 0 .. nev - 1] in index order (device arrays)
 void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t s);
 void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s);        // strict upper <- 0

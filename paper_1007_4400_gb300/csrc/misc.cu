@@ -78,6 +78,45 @@ __global__ void band_energy_kernel(int nprob, int nev, const double* lam, double
   E[p] = s;
 }
 
+// C <- C + D on the lower triangle (diagonal real), mirrored to the upper one; each thread
+// reads only lower entries, so the mirror writes never race with a read
+__global__ void add_lower_herm_kernel(int64_t n, double2* C, int64_t ldc, const double2* D, int64_t ldd) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    if (j > i) continue;
+    double2 v = zadd(C[i * ldc + j], D[i * ldd + j]);
+    if (j == i) {
+      C[i * ldc + i] = make_double2(v.x, 0.0);
+    } else {
+      C[i * ldc + j] = v;
+      C[j * ldc + i] = zconj(v);
+    }
+  }
+}
+
+// Out[i][t] = X[i][idx[t]] (rows x k gather of columns)
+__global__ void gather_cols_kernel(int64_t rows, int k, const double2* X, int64_t ldx, const int64_t* idx,
+                                   double2* Out, int64_t ldo) {
+  const int64_t total = rows * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    const int t = (int)(e % k);
+    Out[i * ldo + t] = X[i * ldx + idx[t]];
+  }
+}
+
+// Out[t][j] = X[idx[t]][j] (k x cols gather of rows)
+__global__ void gather_rows_kernel(int k, int64_t cols, const double2* X, int64_t ldx, const int64_t* idx,
+                                   double2* Out, int64_t ldo) {
+  const int64_t total = (int64_t)k * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / cols);
+    const int64_t j = e % cols;
+    Out[(int64_t)t * ldo + j] = X[idx[t] * ldx + j];
+  }
+}
+
 __global__ void hermitize_avg_kernel(int64_t n, double2* C, int64_t ldc) {
   int64_t total = n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -188,6 +227,23 @@ void hermitize_lower(int64_t n, double2* C, int64_t ldc, cudaStream_t s) {
 }
 void hermitize_scale_lower(int64_t n, double2* C, int64_t ldc, const double* scale, double sign, cudaStream_t s) {
   hermitize_scale_lower_kernel<<<grid_for(n * n), kThreads, 0, s>>>(n, C, ldc, scale, sign);
+  LAUNCH_NOTE(1);
+}
+void add_lower_herm(int64_t n, double2* C, int64_t ldc, const double2* D, int64_t ldd, cudaStream_t s) {
+  if (n <= 0) return;
+  add_lower_herm_kernel<<<grid_for(n * n), kThreads, 0, s>>>(n, C, ldc, D, ldd);
+  LAUNCH_NOTE(1);
+}
+void gather_cols(int64_t rows, int k, const double2* X, int64_t ldx, const int64_t* idx, double2* Out, int64_t ldo,
+                 cudaStream_t s) {
+  if (rows <= 0 || k <= 0) return;
+  gather_cols_kernel<<<grid_for(rows * k), kThreads, 0, s>>>(rows, k, X, ldx, idx, Out, ldo);
+  LAUNCH_NOTE(1);
+}
+void gather_rows(int k, int64_t cols, const double2* X, int64_t ldx, const int64_t* idx, double2* Out, int64_t ldo,
+                 cudaStream_t s) {
+  if (cols <= 0 || k <= 0) return;
+  gather_rows_kernel<<<grid_for((int64_t)k * cols), kThreads, 0, s>>>(k, cols, X, ldx, idx, Out, ldo);
   LAUNCH_NOTE(1);
 }
 void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t s) {

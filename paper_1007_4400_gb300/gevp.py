@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True):
         L.gevp_spectral_bounds.argtypes = [vp, i64, vp, i64, i32, i32, C.POINTER(f64)]
         L.gevp_energy_backward.argtypes = [vp, i64, i32, vp, i64, vp, vp, vp, vp, i64]
         L.gevp_band_energy.argtypes = [vp, i32, i32, vp, vp]
+        L.gevp_reduce_update.argtypes = [vp, i64, vp, i64, i32, vp, i64, i32, C.POINTER(i64), vp, i64, i32,
+                                         C.POINTER(i64)]
         L.gevp_probe_peaks.argtypes = [vp, C.POINTER(f64)]
         L.gevp_matrix_variation.argtypes = [vp, i64, vp, i64, vp, i64, i32, C.POINTER(f64), C.POINTER(f64),
                                             C.POINTER(i64), vp]
@@ -128,7 +130,8 @@ def load(build_if_missing: bool = True):
         L.gevp_kernel_launches.restype = i64
         for name in ("gevp_create", "gevp_destroy", "gevp_set_stream", "gevp_reduce", "gevp_solve_sequence",
                      "gevp_solve_sequence_host", "gevp_solve_batched", "gevp_chebyshev_filter", "gevp_cholqr2", "gevp_rayleigh_ritz",
-                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_band_energy", "gevp_probe_peaks",
+                     "gevp_heev_small", "gevp_spectral_bounds", "gevp_energy_backward", "gevp_band_energy", "gevp_reduce_update",
+                     "gevp_probe_peaks",
                      "gevp_matrix_variation", "gevp_deviation_angles", "gevp_assign_min_cost",
                      "gevp_zgemm_emulated", "gevp_reduce_emulated", "gevp_kernel_timing",
                      "gevp_kernel_timing_read"):
@@ -412,6 +415,22 @@ def spectral_bounds(Cm: torch.Tensor, k: int = 32, count: int = 0):
     st = load().gevp_spectral_bounds(h, Cm.shape[0], _ptr(Cm), Cm.stride(0), int(k), int(count), out)
     _check(st, h)
     return list(out)
+
+
+def reduce_update(Cm: torch.Tensor, B: torch.Tensor, dA: torch.Tensor, rows, slices: int = 8,
+                  reuse_factor: bool = False) -> torch.Tensor:
+    """Cm (in place) <- Cm + L^-1 dA L^-H for a change dA of A confined to the given rows
+    and columns (gevp_reduce_update); returns Cm."""
+    _mat(Cm, "C"); _mat(B, "B"); _mat(dA, "dA")
+    n = Cm.shape[0]
+    h = _handle(Cm.device)
+    rs = [int(r) for r in rows]
+    ra = (C.c_int64 * max(len(rs), 1))(*rs)
+    info = C.c_int64(0)
+    st = load().gevp_reduce_update(h, n, _ptr(B), B.stride(0), 1 if reuse_factor else 0, _ptr(dA), dA.stride(0),
+                                   len(rs), ra, _ptr(Cm), Cm.stride(0), int(slices), C.byref(info))
+    _check(st, h)
+    return Cm
 
 
 def energy_backward(X: torch.Tensor, Lambda: torch.Tensor, gE=1.0):
