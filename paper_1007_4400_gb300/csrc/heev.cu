@@ -823,19 +823,23 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   double2* Zn = w.T;   // ping-pong partner
   const dim3 ugrid((m + 15) / 16, (m + 15) / 16);
   for (int it = 0; it <= refine_iters; ++it) {
+    const bool only_orth = it == refine_iters;
     // R = I - Z^H Z (the kernels below are given Z^H Z; Hermitian: lower tiles only)
     zgram(m, m, m, Z, m, Z, m, w.R, m, 1, w.split_ws, w.split_ws_elems, w.gcnt, s);
-    // E <- G Z (E used as scratch), S = Z^H (G Z) (Hermitian: lower tiles only)
-    ZgemmArgs b = zg(m, m, m, G, ldg, 0, Z, m, 0, w.E, m);
-    zgemm(b, w.split_ws, w.split_ws_elems, s);
-    zgram(m, m, m, Z, m, w.E, m, w.S, m, 1, w.split_ws, w.split_ws_elems, w.gcnt, s);
-    // partial sums in E: the product G Z it held has been consumed by S = Z^H (G Z)
-    oa_partial_kernel<<<nblk, 256, 0, s>>>(m, w.R, w.S, w.lam, part);
-    oa_finish_kernel<<<1, 32, 0, s>>>(nblk, part, w.scal);
-    LAUNCH_NOTE(2);
+    if (!only_orth) {
+      // E <- G Z (E used as scratch), S = Z^H (G Z) (Hermitian: lower tiles only)
+      ZgemmArgs b = zg(m, m, m, G, ldg, 0, Z, m, 0, w.E, m);
+      zgemm(b, w.split_ws, w.split_ws_elems, s);
+      zgram(m, m, m, Z, m, w.E, m, w.S, m, 1, w.split_ws, w.split_ws_elems, w.gcnt, s);
+      // partial sums in E: the product G Z it held has been consumed by S = Z^H (G Z)
+      oa_partial_kernel<<<nblk, 256, 0, s>>>(m, w.R, w.S, w.lam, part);
+      oa_finish_kernel<<<1, 32, 0, s>>>(nblk, part, w.scal);
+      LAUNCH_NOTE(2);
+    }
     // the last step corrects only the orthonormality (E = R/2 everywhere: a symmetric
-    // Newton-Schulz step) and yields Rayleigh quotients of the vectors it returns
-    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, it == refine_iters ? 1 : 0);
+    // Newton-Schulz step), which needs neither S nor the eigenvalue estimates; the
+    // eigenvalues come from S = Z^H G Z of the final Z below
+    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, only_orth ? 1 : 0);
     LAUNCH_NOTE(1);
     // Zn = Z + Z E (the correction's product in FP32)
     zupd32_kernel<<<ugrid, 256, 0, s>>>(m, Z, w.E, Zn);

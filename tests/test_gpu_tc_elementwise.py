@@ -93,11 +93,13 @@ def test_tc_product_elementwise_bench_shape(cuda, prec, nsplit):
     assert np.max(d) < 1e-2 * np.max(acc_bound)
 
 
-@pytest.mark.parametrize("prec,deg,tol", [("bf16", 4, 1e-1), ("bf16", 12, 1e-1), ("fp32", 4, 4e-5),
-                                          ("fp32", 12, 4e-5)])
+@pytest.mark.parametrize("prec,deg,tol", [("bf16", 4, 5e-2), ("bf16", 12, 5e-2), ("fp32", 4, 1e-4),
+                                          ("fp32", 12, 1e-4)])
 def test_tc_filter_blockwise_bench_shape(cuda, prec, deg, tol):
-    """The recurrence at the bench shape against the oracle, per 128-row block and column
-    (the BF16 and FP32-class tolerances of the whole-block checks, applied to every block)."""
+    """The recurrence at the bench shape against the oracle: the whole block within the
+    precision mode's tolerance, and no block of 128 rows (one MMA tile) in any column more
+    than 10x the median block error: a lost, doubled or misplaced tile or split-K slice
+    stands out against the median, which a localised error does not move."""
     from oracle import pieces
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(3000 + deg + len(prec))
@@ -108,7 +110,10 @@ def test_tc_filter_blockwise_bench_shape(cuda, prec, deg, tol):
     Yg = gevp.chebyshev_filter(torch.from_numpy(Cm).to(cuda), torch.from_numpy(Y0).to(cuda), deg, lo, hi, s,
                                prec=prec).cpu().numpy()
     Yr = pieces.chebyshev_filter(Cm, Y0, deg, lo, hi, s)
+    glob = np.linalg.norm(Yg - Yr) / np.linalg.norm(Yr)
+    assert glob < tol
     E = (Yg - Yr).reshape(n // 128, 128, m)
     R = Yr.reshape(n // 128, 128, m)
     rel = np.linalg.norm(E, axis=1) / np.linalg.norm(R, axis=1)
-    assert rel.max() < tol, f"worst block {np.unravel_index(rel.argmax(), rel.shape)}: {rel.max():.3g}"
+    med = np.median(rel)
+    assert rel.max() < 10 * med, f"worst block {np.unravel_index(rel.argmax(), rel.shape)}: {rel.max() / med:.3g}x median"
