@@ -320,9 +320,12 @@ __global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, flo
 // of one thread-block cluster. G lives in the CTAs' shared memory as row bands (two
 // buffers: a round reads one and writes the other, so CTAs still computing the round's
 // rotations never see rotated entries), read and written through distributed shared
-// memory; one cluster barrier per round instead of one CTA doing every 2 x 2 block. The
-// arithmetic of every element is that of jacobi32_body, so the results are identical. Z
-// stays in global memory (read through L2). Gin (m x m) is read, not modified.
+// memory; one cluster barrier per round instead of one CTA doing every 2 x 2 block. Z is
+// held as row bands too: the update Z <- Z U mixes two columns within each row, so every
+// CTA rotates its own rows in its own shared memory (two thirds of a round's tasks, which
+// no longer go through L2), and writes its band to Z at the end. The arithmetic of every
+// element is that of jacobi32_body, so the results are identical. Gin (m x m) is read,
+// not modified.
 constexpr int kJC = 8;
 constexpr int kJClusterMax = 256;
 
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
                                                                  int* perm, int max_sweeps) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
-  extern __shared__ float2 jband[];   // [2][mb][m]
+  extern __shared__ float2 jband[];   // [2][mb][m] G bands, then [mb][m] the Z band
   __shared__ float4 U[512];
   __shared__ int PQ[512][2];
   __shared__ float red[32];
@@ -350,10 +353,11 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
     jband[e] = r < m ? Gin[r * m + (e % m)] : make_float2(0.f, 0.f);
   }
   const int gtid = rank * JT + tid, gsz = kJC * JT;
-  for (int e = gtid; e < m * m; e += gsz) Z[e] = make_float2((e / m) == (e % m) ? 1.f : 0.f, 0.f);
+  const int rows = max(0, min(mb, m - r0));
+  float2* zband = jband + 2 * mb * m;   // own rows r0 .. r0 + rows - 1 of Z
+  for (int e = tid; e < rows * m; e += JT) zband[e] = make_float2((r0 + e / m) == (e % m) ? 1.f : 0.f, 0.f);
   const int np = (m % 2) ? m + 1 : m;
   const int npairs = np / 2;
-  const int rows = max(0, min(mb, m - r0));
   float f = 0.f;
   for (int e = tid; e < rows * m; e += JT) { float2 g = jband[e]; f += g.x * g.x + g.y * g.y; }
   f = block_sum(f, red);
@@ -387,8 +391,20 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
       const GBand Ac{bandp[cur], m, mb}, An{bandp[cur ^ 1], m, mb};
       for (int k = tid; k < npairs; k += JT) jacobi_pair_params(Ac, m, np, step, k, U, PQ);
       __syncthreads();
-      for (int e = gtid; e < npairs * npairs + m * npairs; e += gsz)
-        jacobi_apply<GBand, true>(Ac, An, Z, m, npairs, e, U, PQ);
+      for (int e = gtid; e < npairs * npairs; e += gsz) jacobi_apply<GBand, true>(Ac, An, Z, m, npairs, e, U, PQ);
+      // Z <- Z U on the own rows (columns r, s of each pair), in this CTA's shared memory
+      for (int t = tid; t < rows * npairs; t += JT) {
+        const int il = t / npairs, b = t % npairs;
+        const int r = PQ[b][0], sc = PQ[b][1];
+        if (sc >= m) continue;
+        const float4 u = U[b];
+        const float c = u.x, sn = u.y;
+        const float2 phc = make_float2(u.z, -u.w);
+        float2* zrow = zband + il * m;
+        const float2 zr = zrow[r], zs = cmulf(zrow[sc], phc);
+        zrow[r] = make_float2(c * zr.x - sn * zs.x, c * zr.y - sn * zs.y);
+        zrow[sc] = make_float2(sn * zr.x + c * zs.x, sn * zr.y + c * zs.y);
+      }
       cl.sync();
       cur ^= 1;
     }
@@ -406,6 +422,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
       w[r] = wi;
     }
   }
+  for (int e = tid; e < rows * m; e += JT) Z[(int64_t)r0 * m + e] = zband[e];
   // no CTA leaves while rank 0 may still read its shared memory
   cl.sync();
 }
@@ -742,11 +759,11 @@ bool jacobi32_coop(int m, float2* G, float2* Gb, float2* Z, float* w, int* perm,
 bool jacobi32_cluster(int m, const float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
   if (m < 32 || m > kJClusterMax) return false;
   const int mb = (m + kJC - 1) / kJC;
-  const size_t smem = (size_t)2 * mb * m * sizeof(float2);
+  const size_t smem = (size_t)3 * mb * m * sizeof(float2);
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(jacobi32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * ((kJClusterMax + kJC - 1) / kJC) * kJClusterMax * sizeof(float2))) !=
+                             (int)(3 * ((kJClusterMax + kJC - 1) / kJC) * kJClusterMax * sizeof(float2))) !=
         cudaSuccess) {
       cudaGetLastError();
       return false;
