@@ -25,7 +25,11 @@
 //       S[i, e] -= A[i, j] S[j, e] / a_jj         (e <= j; the inverse, L X = I, right-looking)
 //     L[i, j] = A[i, j] / sqrt(a_jj) and (L^-1)[i, e] = S[i, e] / sqrt(a_ii) are read off at
 //     the end. Within a step the reads (column j, row j, the pivot) and the writes
-//     (columns > j of A, rows > j of S) never meet, so one barrier per step suffices.
+//     (columns > j of A, rows > j of S) never meet, so one barrier per step suffices. The
+//     barrier is split: a step first updates what the next step reads (column j + 1 with
+//     the next pivot, row j + 1 of S), arrives, updates the rest while the other CTAs catch
+//     up, and waits only before the next gather; the gathered values are double-buffered,
+//     so a thread gathering step j + 1 never overwrites what another still reads for j.
 //   The output Li = L^-1 D (columns scaled by D) makes Y Li^H = Y D L^-H, the orthonormal
 //   factor of one CholQR pass, a single product. A non-positive pivot stops the cluster
 //   (every CTA reads the same pivot, so the decision is uniform) and sets *info to its
@@ -97,7 +101,11 @@ __global__ void __launch_bounds__(256) zgram_kernel(int64_t n, int mx, int my, c
 }
 
 constexpr int CT = 256;          // threads per cholinv CTA
-constexpr int kCholInvMax = 320; // largest order (shared-memory bound at 16 CTAs)
+constexpr int kCholInvMax = 288; // largest order (shared-memory bound at 16 CTAs)
+
+// split cluster barrier: arrive (release) and, later, wait (acquire) for the phase
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 template <int P>
 __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const double2* __restrict__ W, int64_t ldw,
@@ -106,9 +114,11 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double2 csm[];
-  __shared__ double2 cbuf[kCholInvMax];   // column j of A (raw), rows > j
-  __shared__ double2 xbuf[kCholInvMax];   // row j of S (raw), columns <= j
-  __shared__ double2 cs[kCholInvMax / 8]; // own rows' A[i, j] / a_jj
+  // gathered values of step j in buffer j & 1: a thread may gather step j + 1 while another
+  // still finishes step j's update
+  __shared__ double2 cbuf[2][kCholInvMax];   // column j of A (raw), rows > j
+  __shared__ double2 xbuf[2][kCholInvMax];   // row j of S (raw), columns <= j
+  __shared__ double2 cs[2][kCholInvMax / 8]; // own rows' -A[i, j] / a_jj
   __shared__ double dsc[kCholInvMax];     // D
   __shared__ double piv[kCholInvMax];     // sqrt(a_jj)
   __shared__ double2 pinfo[kCholInvMax / 8];   // own rows: (pivot a_ii, rsqrt(a_ii)) once final
@@ -151,25 +161,31 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
   cl.sync();
   bool failed = false;
   for (int j = 0; j < m; ++j) {
-    const int oj = j % P, tjj = j / P;
+    const int oj = j % P, tjj = j / P, bsel = j & 1;
+    double2* cb = cbuf[bsel];
+    double2* xb = xbuf[bsel];
+    double2* cm = cs[bsel];
     // own rows below the pivot: i = rank + P t > j, t in [t0, t1)
     const int t0 = j >= rank ? (j - rank) / P + 1 : 0;
     int t1 = R;
     while (t1 > t0 && rank + P * (t1 - 1) >= m) --t1;
     const int nr = t1 - t0;
-    // gather column j and row j of the inverse (raw values, final after step j - 1); the
-    // threads of own rows also form the row's multiplier -A[i][j] / a_jj from the pivot's
-    // reciprocal square root, prepared by the pivot's owner when it became final
+    // everything step j reads is final once every CTA has arrived after step j - 1's
+    // first part (column j, row j of the inverse, the pivot)
+    if (j > 0) cluster_wait();
+    // gather column j and row j of the inverse (raw values); the threads of own rows also
+    // form the row's multiplier -A[i][j] / a_jj from the pivot's reciprocal square root,
+    // prepared by the pivot's owner when it became final
     for (int l = tid; l < m; l += CT) {
       if (l > j) {
         const double2 c = rA[l % P][(l / P) * m + j];
-        cbuf[l] = c;
+        cb[l] = c;
         if (l % P == rank) {
           const double ri = rPI[oj][tjj].y;
-          cs[l / P - t0] = zscale(c, -(ri * ri));
+          cm[l / P - t0] = zscale(c, -(ri * ri));
         }
       } else {
-        xbuf[l] = rS[oj][tjj * m + l];
+        xb[l] = rS[oj][tjj * m + l];
       }
     }
     if (tid == 0) {
@@ -184,27 +200,48 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
       failed = true;
       break;
     }
+    // first part: what step j + 1 reads. Column j + 1 of the own rows below the pivot (with
+    // the next pivot and its reciprocal square root), and row j + 1 of the inverse if it is
+    // an own row
+    const int own_next = ((j + 1) % P == rank && j + 1 < m) ? (j + 1) / P : -1;
+    const int nfirst = nr + (own_next >= 0 ? j + 1 : 0);
+    for (int q = tid; q < nfirst; q += CT) {
+      if (q < nr) {
+        const int t = t0 + q, e = j + 1;
+        double2 v = Arow[t * m + e];
+        zfma(v, cm[q], zconj(cb[e]));
+        Arow[t * m + e] = v;
+        if (rank + P * t == j + 1) pinfo[t] = make_double2(v.x, v.x > 0.0 ? rsqrt(v.x) : 0.0);
+      } else {
+        const int e = q - nr, t = own_next;
+        double2 v = Srow[t * m + e];
+        zfma(v, cm[t - t0], xb[e]);
+        Srow[t * m + e] = v;
+      }
+    }
+    cluster_arrive();
+    // the rest of the update, while the other CTAs finish their first parts
     for (int idx = tid; idx < nr * m; idx += CT) {
       const int tt = idx / m, e = idx % m, t = t0 + tt, i = rank + P * t;
-      if (e > i) continue;
-      const double2 li = cs[tt];
+      if (e > i || e == j + 1 || (i == j + 1 && e <= j)) continue;
+      const double2 li = cm[tt];
       if (e <= j) {
         double2 v = Srow[t * m + e];
-        zfma(v, li, xbuf[e]);
+        zfma(v, li, xb[e]);
         Srow[t * m + e] = v;
       } else {
         double2 v = Arow[t * m + e];
-        zfma(v, li, zconj(cbuf[e]));
+        zfma(v, li, zconj(cb[e]));
         Arow[t * m + e] = v;
-        if (e == i && i == j + 1) pinfo[t] = make_double2(v.x, v.x > 0.0 ? rsqrt(v.x) : 0.0);
       }
     }
-    cl.sync();
   }
   if (failed) {
     cl.sync();   // no CTA leaves while another may still read its shared memory
     return;
   }
+  cluster_wait();   // the last step's gathers are over in every CTA
+  __syncthreads();  // and every thread of this one finished its update
   // read off L and L^-1 D for the own rows
   for (int e = tid; e < R * m; e += CT) {
     const int t = e / m, c = e % m, i = rank + P * t;
