@@ -56,7 +56,8 @@ def test_filter_parity(cuda, orc, n, m, deg):
     assert relmax(Yg, Yr) < 1e-12
 
 
-@pytest.mark.parametrize("n,m", [(300, 21), (1000, 48), (517, 140)])
+# m 288: the largest order of the cluster factorisation; m 289: the blocked path
+@pytest.mark.parametrize("n,m", [(300, 21), (1000, 48), (517, 140), (900, 288), (900, 289)])
 def test_cholqr2_parity(cuda, orc, n, m):
     from oracle import pieces
     from paper_1007_4400_gb300 import gevp
