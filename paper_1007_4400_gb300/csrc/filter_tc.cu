@@ -196,13 +196,27 @@ __device__ __forceinline__ void split_store(double v, int nsplit, __nv_bfloat16*
   }
 }
 
+// The same pieces for a value that is already FP32, in FP32 arithmetic: each piece is the
+// nearest BF16 of the remainder, and the remainder minus its nearest BF16 is exact in FP32
+// (the two are within a factor of two: Sterbenz), so the pieces equal split_store's
+// bit for bit without FP64 instructions (the FP64 pipe is 1/64 of the FP32 rate here).
+__device__ __forceinline__ void split_store_f32(float v, int nsplit, __nv_bfloat16* base, size_t ps, int64_t e) {
+  float r = v;
+  for (int p = 0; p < nsplit; ++p) {
+    __nv_bfloat16 h = __float2bfloat16_rn(r);
+    base[(size_t)p * ps + e] = h;
+    r -= __bfloat162float(h);
+  }
+}
+
 struct YPlanes {
   __nv_bfloat16* base;   // [piece][part re, im, re+im][ncols_pad][n_pad]
   size_t plane;          // ncols_pad * n_pad
   int nsplit;
   __device__ __forceinline__ void store(int64_t e, float2 y) const {
-    split_store((double)y.x, nsplit, base, 3 * plane, e);
-    split_store((double)y.y, nsplit, base + plane, 3 * plane, e);
+    split_store_f32(y.x, nsplit, base, 3 * plane, e);
+    split_store_f32(y.y, nsplit, base + plane, 3 * plane, e);
+    // the exact sum of two FP32 values needs up to 25 significant bits: split in FP64
     split_store((double)y.x + (double)y.y, nsplit, base + 2 * plane, 3 * plane, e);
   }
 };

@@ -28,6 +28,10 @@ namespace {
 
 constexpr int JT = 1024;   // threads of the Jacobi CTA
 
+// split cluster barrier: arrive (release) and, later, wait (acquire) for the phase
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+
 __device__ __forceinline__ void block_pair(int step, int k, int np, int* p, int* q) {
   // circle method: position 0 fixed, the other np-1 players rotate by one per round
   auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + step) % (np - 1)); };
@@ -323,9 +327,11 @@ __global__ void __launch_bounds__(JT) jacobi32_coop_kernel(int m, float2* G, flo
 // memory; one cluster barrier per round instead of one CTA doing every 2 x 2 block. Z is
 // held as row bands too: the update Z <- Z U mixes two columns within each row, so every
 // CTA rotates its own rows in its own shared memory (two thirds of a round's tasks, which
-// no longer go through L2), and writes its band to Z at the end. The arithmetic of every
-// element is that of jacobi32_body, so the results are identical. Gin (m x m) is read,
-// not modified.
+// no longer go through L2), and writes its band to Z at the end. The round's barrier is
+// split around that work: a CTA arrives once its share of G is written and waits only
+// after rotating its rows of Z (the rotations are double-buffered by round parity). The
+// arithmetic of every element is that of jacobi32_body, so the results are identical. Gin
+// (m x m) is read, not modified.
 constexpr int kJC = 8;
 constexpr int kJClusterMax = 256;
 
@@ -334,8 +340,10 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ float2 jband[];   // [2][mb][m] G bands, then [mb][m] the Z band
-  __shared__ float4 U[512];
-  __shared__ int PQ[512][2];
+  // rotations of round k in buffer k & 1: a thread may compute round k + 1's while another
+  // still rotates its rows of Z with round k's
+  __shared__ float4 U2[2][512];
+  __shared__ int PQ2[2][512][2];
   __shared__ float red[32];
   __shared__ float part[64];          // this CTA's partial sums: [0] ||G||_F^2, [1 + sweep] off-norm
   __shared__ float2* bandp[2][kJC];   // generic addresses of every CTA's two bands
@@ -389,10 +397,14 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
     off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
       const GBand Ac{bandp[cur], m, mb}, An{bandp[cur ^ 1], m, mb};
+      float4* U = U2[step & 1];
+      int(*PQ)[2] = PQ2[step & 1];
       for (int k = tid; k < npairs; k += JT) jacobi_pair_params(Ac, m, np, step, k, U, PQ);
       __syncthreads();
       for (int e = gtid; e < npairs * npairs; e += gsz) jacobi_apply<GBand, true>(Ac, An, Z, m, npairs, e, U, PQ);
-      // Z <- Z U on the own rows (columns r, s of each pair), in this CTA's shared memory
+      // the round's G is written: arrive, and rotate the own rows of Z (columns r, s of each
+      // pair, this CTA's shared memory only) while the other CTAs finish theirs
+      cluster_arrive();
       for (int t = tid; t < rows * npairs; t += JT) {
         const int il = t / npairs, b = t % npairs;
         const int r = PQ[b][0], sc = PQ[b][1];
@@ -405,7 +417,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
         zrow[r] = make_float2(c * zr.x - sn * zs.x, c * zr.y - sn * zs.y);
         zrow[sc] = make_float2(sn * zr.x + c * zs.x, sn * zr.y + c * zs.y);
       }
-      cl.sync();
+      cluster_wait();
       cur ^= 1;
     }
   }
