@@ -355,7 +355,12 @@ gevp_status gevp_zgemm_emulated(gevp_handle h, int opA, int opB, int M, int N, i
 
 /* gevp_reduce with the two n^3 products of the reduction (T = L^-1 tril(A) with the
  * diagonal halved, M = T L^-H, C = M + M^H) emulated as in gevp_zgemm_emulated with
- * `slices` digits. n <= 30720. The same outputs and errors as gevp_reduce. */
+ * `slices` digits, and B factored recursively: for n > 256, n = n1 + n2 with
+ * L21 = A21 L11^-H, L22 L22^H = B22 - L21 L21^H and (L^-1)21 = -L22^-1 L21 L11^-1, the
+ * four off-diagonal products emulated, leaves of order <= 256 factored with their
+ * inverses in one thread-block cluster each. n <= 30720. The same outputs (to FP64
+ * rounding) and errors as gevp_reduce; `info` is the global index of the first
+ * non-positive pivot met. */
 gevp_status gevp_reduce_emulated(gevp_handle h, int64_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
                                  void* L, int64_t ldl, void* C, int64_t ldc, int64_t* info, int slices);
 

@@ -31,9 +31,13 @@
 //     up, and waits only before the next gather; the gathered values are double-buffered,
 //     so a thread gathering step j + 1 never overwrites what another still reads for j.
 //   The output Li = L^-1 D (columns scaled by D) makes Y Li^H = Y D L^-H, the orthonormal
-//   factor of one CholQR pass, a single product. A non-positive pivot stops the cluster
-//   (every CTA reads the same pivot, so the decision is uniform) and sets *info to its
-//   1-based index.
+//   factor of one CholQR pass, a single product; it is also the inverse of D^-1 L, the
+//   Cholesky factor of W itself (shift 0), which is written out on request (the leaves
+//   of the recursive factorisation of B). A non-positive pivot stops the cluster (every
+//   CTA reads the same pivot, so the decision is uniform) and sets *info to its 1-based
+//   index plus a caller's offset. W may share memory with that factor's output: every
+//   CTA reads its rows of W before the first cluster barrier and writes the factor after
+//   the last.
 #include "gevp_internal.cuh"
 #include <cooperative_groups.h>
 #include <algorithm>
@@ -108,9 +112,9 @@ __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 template <int P>
-__global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const double2* __restrict__ W, int64_t ldw,
+__global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const double2* W, int64_t ldw,
                                                                 double shift, double2* Li, int64_t ldi,
-                                                                double2* Lf, int64_t ldl, int* info) {
+                                                                double2* Lf, int64_t ldl, int* info, int info_base) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double2 csm[];
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
     __syncthreads();
     const double a = apiv;   // the same value in every CTA: a uniform decision
     if (!(a > 0.0)) {
-      if (rank == 0 && tid == 0) atomicCAS(info, 0, j + 1);
+      if (rank == 0 && tid == 0) atomicCAS(info, 0, info_base + j + 1);
       failed = true;
       break;
     }
@@ -250,9 +254,10 @@ __global__ void __launch_bounds__(CT, 1) cholinv_cluster_kernel(int m, const dou
     if (c <= i) x = zscale(Srow[e], dsc[c] / piv[i]);
     Li[(int64_t)i * ldi + c] = x;
     if (Lf) {
+      // the factor of W + shift D^-2: D^-1 times the factor of D W D + shift I
       double2 l = make_double2(0.0, 0.0);
-      if (c < i) l = zscale(Arow[e], 1.0 / piv[c]);
-      else if (c == i) l = make_double2(piv[i], 0.0);
+      if (c < i) l = zscale(Arow[e], 1.0 / (piv[c] * dsc[i]));
+      else if (c == i) l = make_double2(piv[i] / dsc[i], 0.0);
       Lf[(int64_t)i * ldl + c] = l;
     }
   }
@@ -265,7 +270,7 @@ size_t cholinv_smem(int m) {
 
 template <int P>
 bool cholinv_launch(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
-                    int64_t ldl, int* info, cudaStream_t s) {
+                    int64_t ldl, int* info, int info_base, cudaStream_t s) {
   const size_t smem = cholinv_smem<P>(m);
   if (smem > 200 * 1024) return false;
   static int ready = 0;   // 0 unknown, 1 usable, -1 not launchable on this device
@@ -313,7 +318,7 @@ bool cholinv_launch(int m, const double2* W, int64_t ldw, double shift, double2*
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, cholinv_cluster_kernel<P>, m, W, ldw, shift, Li, ldi, Lf, ldl, info) !=
+  if (cudaLaunchKernelEx(&cfg, cholinv_cluster_kernel<P>, m, W, ldw, shift, Li, ldi, Lf, ldl, info, info_base) !=
       cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -329,10 +334,10 @@ constexpr int kSMs = 152;
 int cholinv_max_order() { return kCholInvMax; }
 
 bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
-                   int64_t ldl, int* info, cudaStream_t s) {
+                   int64_t ldl, int* info, cudaStream_t s, int info_base) {
   if (m < 1 || m > kCholInvMax) return false;
-  if (cholinv_launch<16>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, s)) return true;
-  return cholinv_launch<8>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, s);
+  if (cholinv_launch<16>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, info_base, s)) return true;
+  return cholinv_launch<8>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, info_base, s);
 }
 
 size_t zgram_counters() { return 4096; }

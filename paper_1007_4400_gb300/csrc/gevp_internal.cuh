@@ -107,6 +107,8 @@ void gather_rows(int k, int64_t cols, const double2* X, int64_t ldx, const int64
 // E[p] = sum of lam[p * nev + 0 .. nev - 1] in index order (device arrays)
 void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t s);
 void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s);        // strict upper <- 0
+void zsub_lower(int64_t n, double2* A, int64_t lda, const double2* P, int64_t ldp, cudaStream_t s);  // A -= P, j <= i
+void zneg(int64_t rows, int64_t cols, double2* X, int64_t ldx, cudaStream_t s);                      // X <- -X
 void zcopy2d(int64_t rows, int64_t cols, const double2* src, int64_t lds, double2* dst, int64_t ldd, cudaStream_t s);
 void zset_identity(int64_t rows, int64_t cols, double2* A, int64_t lda, cudaStream_t s);
 void z_to_c(int64_t rows, int64_t cols, const double2* src, int64_t lds, float2* dst, int64_t ldd, cudaStream_t s);
@@ -169,13 +171,16 @@ void gram_scale(int m, double2* W, int64_t ldw, double* dscale, cudaStream_t s);
 size_t zgram_counters();
 void zgram(int64_t n, int mx, int my, const double2* X, int64_t ldx, const double2* Y, int64_t ldy, double2* G,
            int64_t ldg, int herm, double2* part, size_t part_elems, unsigned* cnt, cudaStream_t s);
-// Li = L^-1 D (lower, ld ldi) and optionally Lf = L, where D W D + shift I = L L^H, W m x m
-// (lower triangle read), D = diag(W)^-1/2 (1 where a diagonal entry is not positive), in
-// one thread-block cluster. *info <- 1-based index of a non-positive pivot (atomicCAS from
-// 0). false: not launchable (m > cholinv_max_order() or no cluster): nothing was enqueued.
+// Li = L^-1 D (lower, ld ldi) and optionally Lf = D^-1 L (lower, upper triangle zeroed;
+// the Cholesky factor of W + shift D^-2, of W itself for shift 0, and Li its inverse),
+// where D W D + shift I = L L^H, W m x m (lower triangle read; Lf may be W), D =
+// diag(W)^-1/2 (1 where a diagonal entry is not positive), in one thread-block cluster.
+// *info <- info_base + the 1-based index of a non-positive pivot (atomicCAS from 0;
+// nothing else is written then). false: not launchable (m > cholinv_max_order() or no
+// cluster): nothing was enqueued.
 int cholinv_max_order();
 bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
-                   int64_t ldl, int* info, cudaStream_t s);
+                   int64_t ldl, int* info, cudaStream_t s, int info_base = 0);
 
 // ---------------------------------------------------------------- backward
 // GA = gE X X^H, GB = -gE X diag(lam) X^H (lower tiles by GEMM, then Hermitian completion

@@ -132,6 +132,27 @@ __global__ void hermitize_avg_kernel(int64_t n, double2* C, int64_t ldc) {
   }
 }
 
+// A <- A - P on the lower triangle (j <= i) of an n x n block
+__global__ void zsub_lower_kernel(int64_t n, double2* A, int64_t lda, const double2* P, int64_t ldp) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    if (j <= i) {
+      const double2 a = A[i * lda + j], p = P[i * ldp + j];
+      A[i * lda + j] = make_double2(a.x - p.x, a.y - p.y);
+    }
+  }
+}
+
+__global__ void zneg_kernel(int64_t rows, int64_t cols, double2* X, int64_t ldx) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+    const double2 v = X[i * ldx + j];
+    X[i * ldx + j] = make_double2(-v.x, -v.y);
+  }
+}
+
 __global__ void zero_upper_kernel(int64_t n, double2* L, int64_t ldl) {
   int64_t total = n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -252,6 +273,16 @@ void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t 
 }
 void hermitize_avg(int64_t n, double2* C, int64_t ldc, cudaStream_t s) {
   hermitize_avg_kernel<<<grid_for(n * n), kThreads, 0, s>>>(n, C, ldc);
+  LAUNCH_NOTE(1);
+}
+void zsub_lower(int64_t n, double2* A, int64_t lda, const double2* P, int64_t ldp, cudaStream_t s) {
+  if (n <= 0) return;
+  zsub_lower_kernel<<<grid_for(n * n), kThreads, 0, s>>>(n, A, lda, P, ldp);
+  LAUNCH_NOTE(1);
+}
+void zneg(int64_t rows, int64_t cols, double2* X, int64_t ldx, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  zneg_kernel<<<grid_for(rows * cols), kThreads, 0, s>>>(rows, cols, X, ldx);
   LAUNCH_NOTE(1);
 }
 void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s) {

@@ -314,12 +314,54 @@ __device__ __forceinline__ double2 oz_entry(const double2* X, int64_t ldx, int r
   return oz_masked(X[(int64_t)r * ldx + k], r, k, conj, mask);
 }
 
-__device__ __forceinline__ bool oz_finite(double2 v) {
-  return fabs(v.x) <= 1.7976931348623157e308 && fabs(v.y) <= 1.7976931348623157e308;
+// The splitting works on the IEEE-754 fields with integer instructions only: one SM
+// retires about two FP64 operations per clock on this part, and a conversion, a scaling
+// and a maximum per entry on the FP64 pipe made the splitter several times slower than
+// its memory traffic.
+//
+// |v| as an ordered integer key: for finite values the order of the keys is the order of
+// the magnitudes; an exponent field of all ones (Inf or NaN) is reported as non-finite.
+__device__ __forceinline__ unsigned long long oz_abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ bool oz_key_finite(unsigned long long key) { return (key >> 52) != 0x7FF; }
+
+// floor(log2 |x|) of the value with magnitude key `key` (> 0, finite), as ilogb.
+__device__ __forceinline__ int oz_key_ilogb(unsigned long long key) {
+  const int E = (int)(key >> 52);
+  return E != 0 ? E - 1023 : (63 - __clzll((long long)key)) - 1074;
 }
 
-__device__ __forceinline__ void oz_digits(double x, int shift, int S, __nv_bfloat16* out, size_t plane) {
-  long long q = __double2ll_rn(ldexp(x, shift));
+// round(x 2^shift) to the nearest integer, ties to even, for finite x with
+// |x 2^shift| < 2^62: x = M 2^k' with the integer significand M < 2^53, so the result is
+// M shifted left, or shifted right with the dropped bits deciding the rounding. The same
+// value as converting ldexp(x, shift) with round-to-nearest-even, without FP64
+// instructions. A non-finite x gives 0 (its row is reported as bad).
+__device__ __forceinline__ long long oz_round_scaled(double x, int shift) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0x7FF) return 0;
+  unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+  int k = shift - 1074;                    // subnormal: x = M 2^-1074
+  if (E != 0) {
+    M |= 1ull << 52;
+    k = E - 1075 + shift;
+  }
+  unsigned long long q;
+  if (k >= 0) {
+    q = M << k;
+  } else if (k < -63) {
+    q = 0;                                 // |x 2^shift| < 2^-10
+  } else {
+    const int r = -k;
+    q = M >> r;
+    const unsigned long long rem = M & ((1ull << (r - 1) << 1) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ void oz_digits_q(long long q, int S, __nv_bfloat16* out, size_t plane) {
   for (int s = S - 1; s >= 1; --s) {
     const long long d = ((q + 64) & 127) - 64;
     out[(size_t)s * plane] = __int2bfloat16_rn((int)d);
@@ -328,30 +370,36 @@ __device__ __forceinline__ void oz_digits(double x, int shift, int S, __nv_bfloa
   out[0] = __int2bfloat16_rn((int)q);
 }
 
+// the digits of x, of -x (npl = 3: the negated imaginary part) from the same rounding:
+// rounding to nearest even is odd-symmetric, so round(-x 2^shift) = -round(x 2^shift)
+__device__ __forceinline__ void oz_digits(double x, int shift, int S, __nv_bfloat16* out, size_t plane) {
+  oz_digits_q(oz_round_scaled(x, shift), S, out, plane);
+}
+
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, const double2* X, int64_t ldx, int conj,
                                                             int mask, int S, int npl, int rows_pad, int k_pad,
                                                             __nv_bfloat16* planes, int* ex, int* bad,
                                                             const int* active) {
   if (active && *active == 0) return;
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int r = blockIdx.x;
-  double mx = 0.0;
+  unsigned long long mx = 0;   // largest magnitude key of the finite entries
   bool nonfinite = false;
   if (r < rows)
     for (int k = threadIdx.x; k < K; k += 256) {
       const double2 v = oz_entry(X, ldx, r, k, K, conj, mask);
-      // NaN or Inf (tested per part: fmax would drop a NaN)
-      if (!oz_finite(v)) nonfinite = true;
-      else mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long kx = oz_abs_key(v.x), ky = oz_abs_key(v.y);
+      if (!oz_key_finite(kx) || !oz_key_finite(ky)) nonfinite = true;
+      else mx = max(mx, max(kx, ky));
     }
   if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicExch(bad, 1);
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   mx = red[0];
-  for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
-  // 2^e > 2 mx: the scaled row lies below 1/2
-  const int e = mx > 0.0 ? ilogb(mx) + 2 : 0;
+  for (int w = 1; w < 8; ++w) mx = max(mx, red[w]);
+  // 2^e > 2 max|entry|: the scaled row lies below 1/2
+  const int e = mx > 0 ? oz_key_ilogb(mx) + 2 : 0;
   if (threadIdx.x == 0 && r < rows) ex[r] = e;
   const int shift = 7 * S - e;
   const size_t plane = (size_t)rows_pad * k_pad;
@@ -359,9 +407,10 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(int rows, int K, con
   for (int k = threadIdx.x; k < k_pad; k += 256) {
     const double2 v = r < rows ? oz_entry(X, ldx, r, k, K, conj, mask) : make_double2(0.0, 0.0);
     const size_t o = (size_t)r * k_pad + k;
+    const long long qy = oz_round_scaled(v.y, shift);
     oz_digits(v.x, shift, S, planes + o, plane);
-    oz_digits(v.y, shift, S, planes + pstride + o, plane);
-    if (npl == 3) oz_digits(-v.y, shift, S, planes + 2 * pstride + o, plane);
+    oz_digits_q(qy, S, planes + pstride + o, plane);
+    if (npl == 3) oz_digits_q(-qy, S, planes + 2 * pstride + o, plane);
   }
 }
 
@@ -379,23 +428,24 @@ constexpr int OZ_CE_ROWS = 256;             // rows per slice
 __global__ void __launch_bounds__(256) oz_cols_exp_kernel(int R, int K, const double2* X, int64_t ldx, int conj,
                                                           int mask, int* ex, int* bad, const int* active) {
   if (active && *active == 0) return;
-  __shared__ double red[8][OZ_CT];
+  __shared__ unsigned long long red[8][OZ_CT];
   const int j = blockIdx.x * OZ_CT + threadIdx.x;
   const int k0 = blockIdx.y * OZ_CE_ROWS, k1 = min(K, k0 + OZ_CE_ROWS);
-  double mx = 0.0;
+  unsigned long long mx = 0;
   bool nonfinite = false;
   if (j < R)
     for (int k = k0 + threadIdx.y; k < k1; k += 8) {
       const double2 v = oz_masked(X[(int64_t)k * ldx + j], j, k, conj, mask);
-      if (!oz_finite(v)) nonfinite = true;
-      else mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long kx = oz_abs_key(v.x), ky = oz_abs_key(v.y);
+      if (!oz_key_finite(kx) || !oz_key_finite(ky)) nonfinite = true;
+      else mx = max(mx, max(kx, ky));
     }
   if (nonfinite) atomicExch(bad, 1);
   red[threadIdx.y][threadIdx.x] = mx;
   __syncthreads();
   if (threadIdx.y == 0 && j < R) {
-    for (int t = 1; t < 8; ++t) mx = fmax(mx, red[t][threadIdx.x]);
-    if (mx > 0.0) atomicMax(&ex[j], ilogb(mx) + 2);
+    for (int t = 1; t < 8; ++t) mx = max(mx, red[t][threadIdx.x]);
+    if (mx > 0) atomicMax(&ex[j], oz_key_ilogb(mx) + 2);
   }
 }
 
@@ -423,9 +473,10 @@ __global__ void __launch_bounds__(256) oz_cols_digits_kernel(int R, int K, const
     const int e = j < R ? ex[j] : 0;
     const int shift = 7 * S - (e == kExpNone ? 0 : e);
     const size_t o = (size_t)j * k_pad + k;
+    const long long qy = oz_round_scaled(v.y, shift);
     oz_digits(v.x, shift, S, planes + o, plane);
-    oz_digits(v.y, shift, S, planes + pstride + o, plane);
-    if (npl == 3) oz_digits(-v.y, shift, S, planes + 2 * pstride + o, plane);
+    oz_digits_q(qy, S, planes + pstride + o, plane);
+    if (npl == 3) oz_digits_q(-qy, S, planes + 2 * pstride + o, plane);
   }
 }
 

@@ -117,6 +117,45 @@ def test_reduce_emulated_vs_oracle(cuda, orc, n):
     assert np.array_equal(C, C.conj().T)
 
 
+# the emulated mode factors B recursively: leaves of order <= 256 in one cluster launch,
+# the off-diagonal blocks of L and L^-1 from emulated products. 256: one leaf; 300: one
+# split (128 + 172); 700 and 1100: two and three levels with ragged leaves.
+@pytest.mark.parametrize("n", [256, 300, 700, 1100])
+def test_emulated_factor_vs_oracle(cuda, orc, n):
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(4100 + n)
+    A, B = rand_herm(rng, n), rand_hpd(rng, n, 1e3)
+    L, C = gevp.reduce(T(A, cuda), T(B, cuda), slices=8)
+    L = L.cpu().numpy()
+    Lr, info = orc.potrf(B)
+    assert info == 0
+    assert np.array_equal(np.triu(L, 1), np.zeros_like(L))
+    assert np.abs(L - Lr).max() <= 1e-13 * np.abs(Lr).max()
+    # the reduction used the recursive form's L^-1: C against the oracle's
+    Cr = orc.reduce(A, Lr)
+    assert np.abs(C.cpu().numpy() - Cr).max() <= 1e-12 * np.abs(Cr).max()
+
+
+@pytest.mark.parametrize("n,k", [(600, 400), (600, 17), (200, 150)])
+def test_emulated_factor_not_hpd(cuda, n, k):
+    """A non-positive pivot in a later leaf, in the first leaf and in a single leaf: the
+    global 1-based index is reported, the handle stays usable."""
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(4200 + n + k)
+    B = rand_hpd(rng, n, 10.0)
+    B[k, :] = 0.0
+    B[:, k] = 0.0
+    B[k, k] = -1.0
+    A = np.eye(n, dtype=np.complex128)
+    with pytest.raises(gevp.GevpError) as e:
+        gevp.reduce(T(A, cuda), T(B, cuda), slices=8)
+    assert e.value.status == 2 and f"pivot {k + 1}" in str(e.value)
+    B2 = rand_hpd(rng, n, 10.0)
+    L, _ = gevp.reduce(T(A, cuda), T(B2, cuda), slices=8)
+    Lh = L.cpu().numpy()
+    assert np.abs(Lh @ Lh.conj().T - B2).max() <= 1e-13 * np.abs(B2).max() * n
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_solver_with_emulated_reduction(cuda, orc, prec):
     from paper_1007_4400_gb300 import gevp, synth
