@@ -109,6 +109,7 @@ void band_energy(int nprob, int nev, const double* lam, double* E, cudaStream_t 
 void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s);        // strict upper <- 0
 void zsub_lower(int64_t n, double2* A, int64_t lda, const double2* P, int64_t ldp, cudaStream_t s);  // A -= P, j <= i
 void zneg(int64_t rows, int64_t cols, double2* X, int64_t ldx, cudaStream_t s);                      // X <- -X
+void eye_deviation(int m, const double2* G, int64_t ldg, double* out_dev, cudaStream_t s);  // max |G - I|
 void zcopy2d(int64_t rows, int64_t cols, const double2* src, int64_t lds, double2* dst, int64_t ldd, cudaStream_t s);
 void zset_identity(int64_t rows, int64_t cols, double2* A, int64_t lda, cudaStream_t s);
 void z_to_c(int64_t rows, int64_t cols, const double2* src, int64_t lds, float2* dst, int64_t ldd, cudaStream_t s);

@@ -153,6 +153,27 @@ __global__ void zneg_kernel(int64_t rows, int64_t cols, double2* X, int64_t ldx)
   }
 }
 
+// out[0] = max_ij |G_ij - delta_ij| over an m x m block (one CTA; fixed reduction order)
+__global__ void __launch_bounds__(1024) eye_dev_kernel(int m, const double2* G, int64_t ldg, double* out) {
+  __shared__ double red[32];
+  double mx = 0.0;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t e = threadIdx.x; e < mm; e += blockDim.x) {
+    const int64_t i = e / m, j = e % m;
+    double2 v = G[i * ldg + j];
+    if (i == j) v.x -= 1.0;
+    mx = fmax(mx, sqrt(v.x * v.x + v.y * v.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    out[0] = t;
+  }
+}
+
 __global__ void zero_upper_kernel(int64_t n, double2* L, int64_t ldl) {
   int64_t total = n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -283,6 +304,11 @@ void zsub_lower(int64_t n, double2* A, int64_t lda, const double2* P, int64_t ld
 void zneg(int64_t rows, int64_t cols, double2* X, int64_t ldx, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return;
   zneg_kernel<<<grid_for(rows * cols), kThreads, 0, s>>>(rows, cols, X, ldx);
+  LAUNCH_NOTE(1);
+}
+void eye_deviation(int m, const double2* G, int64_t ldg, double* out_dev, cudaStream_t s) {
+  if (m <= 0) return;
+  eye_dev_kernel<<<1, 1024, 0, s>>>(m, G, ldg, out_dev);
   LAUNCH_NOTE(1);
 }
 void zero_upper(int64_t n, double2* L, int64_t ldl, cudaStream_t s) {

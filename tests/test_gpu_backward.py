@@ -45,7 +45,7 @@ def test_autograd_matches_oracle_and_fd(cuda, orc, degenerate):
     GAr, GBr = orc.energy_grad(X_r, lam_r)
     assert np.abs(GA - GAr).max() <= 1e-10 * np.abs(GAr).max()
     assert np.abs(GB - GBr).max() <= 1e-10 * np.abs(GBr).max()
-    assert float(E) == pytest.approx(lam_r.sum(), rel=1e-12, abs=1e-12 * np.abs(lam_r).max())
+    assert float(E.detach()) == pytest.approx(lam_r.sum(), rel=1e-12, abs=1e-12 * np.abs(lam_r).max())
     # central finite differences along random Hermitian directions (step 1e-6)
     rng = np.random.default_rng(11)
     h = 1e-6
