@@ -5,7 +5,9 @@
 //   1. parallel-ordered two-sided Jacobi in FP32 (FP32 runs at 128 FMA per clock per SM),
 //      giving eigenvectors accurate to about 1e-6: one CTA below m = 32, the eight CTAs
 //      of a thread-block cluster sharing G through distributed shared memory up to
-//      m = 256, all SMs (cooperative launch) above;
+//      m = 256, all SMs (cooperative launch) above. The cluster form runs no sweep when
+//      G is already nearly diagonal (the projection of an almost converged block: the
+//      refinement starts from Z = I, see jacobi32_cluster_kernel);
 //   2. Ogita & Aishima's iterative refinement for symmetric/Hermitian eigenvector
 //      matrices (Japan J. Ind. Appl. Math. 35, 2018), which converges quadratically and
 //      consists of four FP64 GEMMs per step spread over all SMs. Pairs closer than the
@@ -336,7 +338,7 @@ constexpr int kJC = 8;
 constexpr int kJClusterMax = 256;
 
 __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const float2* Gin, float2* Z, float* w,
-                                                                 int* perm, int max_sweeps) {
+                                                                 int* perm, int max_sweeps, int may_skip) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ float2 jband[];   // [2][mb][m] G bands, then [mb][m] the Z band
@@ -346,6 +348,8 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
   __shared__ int PQ2[2][512][2];
   __shared__ float red[32];
   __shared__ float part[64];          // this CTA's partial sums: [0] ||G||_F^2, [1 + sweep] off-norm
+  __shared__ float dg[kJClusterMax];  // the diagonal of G
+  __shared__ int coupled;             // this CTA's rows hold a coupling the refinement cannot start from
   __shared__ float2* bandp[2][kJC];   // generic addresses of every CTA's two bands
   const int tid = threadIdx.x;
   const int rank = (int)cl.block_rank();
@@ -368,6 +372,8 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
   const int npairs = np / 2;
   float f = 0.f;
   for (int e = tid; e < rows * m; e += JT) { float2 g = jband[e]; f += g.x * g.x + g.y * g.y; }
+  for (int j = tid; j < m; j += JT) dg[j] = Gin[j * m + j].x;
+  if (tid == 0) coupled = 0;
   f = block_sum(f, red);
   if (tid == 0) part[0] = f;
   cl.sync();
@@ -394,6 +400,32 @@ __global__ void __launch_bounds__(JT, 1) jacobi32_cluster_kernel(int m, const fl
     cl.sync();
     off = cluster_sum(1 + sweep);
     if (off <= tol2 || (off > 0.9f * off_prev && off <= 1e-12f * fro2)) break;
+    if (sweep == 0 && may_skip) {
+      // Nearly diagonal already (the projection of a block that has almost converged):
+      // every coupling at most 1e-3 of its diagonal gap (gaps below eta0 = 1e-6 ||G||_F
+      // counted as eta0: clusters, which FP32 sweeps cannot resolve either), and at most
+      // 1e-5 of it for gaps between eta0 and delta = 2 ||offdiag(G)||_F. The FP64
+      // refinement started from Z = I has the clustering threshold delta in its first step:
+      // it corrects the pairs farther apart than delta there (to about 1e-6), those between
+      // eta0 and delta in its second step (to about 1e-10), and, converging quadratically,
+      // reaches FP64 accuracy in its last step as it would from the sweeps' result; the
+      // clusters go to the exact rotations after it. No sweep is run.
+      const float eta0 = 1e-6f * sqrtf(fro2), delta = 2.f * sqrtf(off);
+      bool c = false;
+      for (int e = tid; e < rows * m; e += JT) {
+        const int i = r0 + e / m, j = e % m;
+        if (i == j) continue;
+        const float2 g = Gc[e];
+        const float gap = fabsf(dg[i] - dg[j]);
+        const float a = hypotf(g.x, g.y);
+        c |= a > 1e-3f * fmaxf(gap, eta0) || (gap > eta0 && gap <= delta && a > 1e-5f * gap);
+      }
+      if (__any_sync(0xffffffffu, c) && (tid & 31) == 0) coupled = 1;
+      cl.sync();
+      int any = 0;
+      for (int r = 0; r < kJC; ++r) any |= *cl.map_shared_rank(&coupled, r);
+      if (!any) break;
+    }
     off_prev = off;
     for (int step = 0; step < np - 1; ++step) {
       const GBand Ac{bandp[cur], m, mb}, An{bandp[cur ^ 1], m, mb};
@@ -572,7 +604,7 @@ __global__ void frob_finish_kernel(int nblk, const double* part, double* out) {
 }
 
 __global__ void oa_update_kernel(int m, const double2* Zg, const double2* S, const double* lam, const double* scal,
-                                 double2* E, int only_orth) {
+                                 double2* E, int only_orth, double emax) {
   int64_t total = (int64_t)m * m;
   double delta = only_orth ? 1e300 : scal[0];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -584,9 +616,10 @@ __global__ void oa_update_kernel(int m, const double2* Zg, const double2* S, con
     if (i != j && fabs(d) > delta) {
       double2 sv = S[e];
       double2 t = make_double2(sv.x + lam[j] * r.x, sv.y + lam[j] * r.y);
-      // first-order correction only where it is small (|E_ij| <= 0.2); larger couplings
-      // are left to the next step, which keeps the iteration from diverging
-      if (sqrt(zabs2(t)) <= 0.2 * fabs(d)) v = make_double2(t.x / d, t.y / d);
+      // first-order correction only where it is small (|E_ij| <= emax); larger couplings
+      // are left to the next step (or to the exact rotations after the last), which keeps
+      // the iteration from diverging
+      if (sqrt(zabs2(t)) <= emax * fabs(d)) v = make_double2(t.x / d, t.y / d);
     }
     E[e] = v;
   }
@@ -768,7 +801,8 @@ bool jacobi32_coop(int m, float2* G, float2* Gb, float2* Z, float* w, int* perm,
 
 // Cluster Jacobi for 32 <= m <= kJClusterMax; false if it cannot be launched (then the
 // caller runs the one-CTA kernel).
-bool jacobi32_cluster(int m, const float2* G, float2* Z, float* w, int* perm, int max_sweeps, cudaStream_t s) {
+bool jacobi32_cluster(int m, const float2* G, float2* Z, float* w, int* perm, int max_sweeps, int may_skip,
+                      cudaStream_t s) {
   if (m < 32 || m > kJClusterMax) return false;
   const int mb = (m + kJC - 1) / kJC;
   const size_t smem = (size_t)3 * mb * m * sizeof(float2);
@@ -794,7 +828,7 @@ bool jacobi32_cluster(int m, const float2* G, float2* Z, float* w, int* perm, in
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, jacobi32_cluster_kernel, m, G, Z, w, perm, max_sweeps) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, jacobi32_cluster_kernel, m, G, Z, w, perm, max_sweeps, may_skip) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -833,7 +867,9 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
   // 32 <= m <= 256 on the eight CTAs of a cluster; larger orders on all SMs (cooperative
   // launch; the FP64 scratch E, unused until the refinement, holds its second FP32 buffer);
   // small ones, or when neither launch is possible, in one CTA
-  bool done = jacobi32_cluster(m, w.G32, w.Z32, w.w32, w.perm, 40, s);
+  // (the sweeps may be skipped for a nearly diagonal G when the refinement has the three
+  // steps that its start from Z = I needs)
+  bool done = jacobi32_cluster(m, w.G32, w.Z32, w.w32, w.perm, 40, refine_iters >= 3 ? 1 : 0, s);
   if (!done && m > kJacobiSmemMax)
     done = jacobi32_coop(m, w.G32, (float2*)w.E, w.Z32, w.w32, w.perm, 40, (float*)(w.scal + 16), s);
   if (!done) {
@@ -868,7 +904,14 @@ void heev_small(int m, const double2* G, int64_t ldg, double* theta, double2* Zo
     // the last step corrects only the orthonormality (E = R/2 everywhere: a symmetric
     // Newton-Schulz step), which needs neither S nor the eigenvalue estimates; the
     // eigenvalues come from S = Z^H G Z of the final Z below
-    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, only_orth ? 1 : 0);
+    // a correction of size e leaves an error of about e^2 for the next step: 0.2 in the
+    // first step and while two or more correcting steps follow, 1e-4 before the last one,
+    // 1e-8 in it, so that what the refinement corrects reaches FP64 accuracy; a pair that
+    // needs more (a near-degenerate pair that the earlier corrections coupled) goes to the
+    // rotations
+    const int rem = refine_iters - 1 - it;
+    const double emax = (rem >= 2 || it == 0) ? 0.2 : (rem == 1 ? 1e-4 : 1e-8);
+    oa_update_kernel<<<blocks, 256, 0, s>>>(m, w.R, w.S, w.lam, w.scal, w.E, only_orth ? 1 : 0, emax);
     LAUNCH_NOTE(1);
     // Zn = Z + Z E (the correction's product in FP32)
     zupd32_kernel<<<ugrid, 256, 0, s>>>(m, Z, w.E, Zn);

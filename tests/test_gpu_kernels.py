@@ -72,7 +72,7 @@ def test_cholqr2_parity(cuda, orc, n, m):
 
 
 # one CTA below 32, the eight-CTA cluster form for 32..256, the cooperative form above
-@pytest.mark.parametrize("m", [1, 2, 3, 17, 31, 32, 33, 64, 140, 159, 161, 200, 255, 256, 257, 301])
+@pytest.mark.parametrize("m", [1, 2, 3, 17, 31, 32, 33, 64, 140, 159, 161, 200, 201, 255, 256, 257, 301])
 def test_heev_small_parity(cuda, orc, m):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(400 + m)
@@ -119,6 +119,33 @@ def test_heev_small_degenerate(cuda, orc):
     P1 = Q[:, 1:4] @ Q[:, 1:4].conj().T
     P2 = Z[:, 1:4] @ Z[:, 1:4].conj().T
     assert np.abs(P1 - P2).max() < 1e-10
+
+
+@pytest.mark.parametrize("m,eps", [(140, 1e-5), (140, 5e-4), (64, 1e-7), (256, 1e-4), (140, 3e-2)])
+def test_heev_small_nearly_diagonal(cuda, orc, m, eps):
+    """The projection of a nearly converged block: a diagonal plus couplings of eps times
+    the gaps, unsorted, with a near-degenerate pair whose coupling is tiny. For eps 1e-5
+    and 1e-7 the cluster eigensolver starts the FP64 refinement from Z = I without FP32
+    sweeps (the couplings are below 1e-3 of the gaps and no gap lies between 1e-6 ||G||_F
+    and 2 ||offdiag G||_F); the larger eps take the sweeps. Both must give the oracle's
+    eigenpairs; in the first the later corrections couple the near-degenerate pair, which
+    the refinement must then leave to the exact rotations."""
+    from paper_1007_4400_gb300 import gevp
+    rng = np.random.default_rng(4300 + m + int(-np.log10(eps)))
+    d = rng.permutation(np.concatenate([np.linspace(-2.0, 2.0, m - 2), [0.3 + 1e-9, 0.3 + 2e-9]]))
+    gaps = np.abs(d[:, None] - d[None, :]) + np.eye(m)
+    E = crandn(rng, m, m)
+    E = 0.5 * (E + E.conj().T)
+    np.fill_diagonal(E, 0.0)
+    G = np.diag(d).astype(np.complex128) + eps * np.minimum(gaps, 1.0) * E / np.abs(E).max()
+    near = np.where(np.abs(d - 0.3) < 1e-8)[0]
+    G[near[0], near[1]] = G[near[1], near[0]] = 1e-12
+    th, Z = gevp.heev_small(T(G, cuda))
+    th, Z = th.cpu().numpy(), Z.cpu().numpy()
+    w, V = orc.heev(G, method="jacobi")
+    assert np.abs(th - w).max() <= 1e-13 * 2.0
+    assert np.abs(Z.conj().T @ Z - np.eye(m)).max() < 1e-13
+    assert np.abs(G @ Z - Z * th).max() <= 1e-13 * 2.0
 
 
 @pytest.mark.parametrize("n,m", [(256, 24), (611, 48)])
