@@ -71,6 +71,7 @@ struct gevp_ctx {
   // B (rows, kept while the factorisation is), the block (columns, per product)
   gevp::OzOperand ozC, ozA, ozB, ozQ, ozLH;
   gevp::OzOperand ozQW, ozZ;                // the Rayleigh-Ritz rotation [Q; W] Z (rows, columns)
+  gevp::OzOperand ozY, ozLiH;               // the CholQR product Y (L^-1 D)^H (rows, conjugated rows)
   gevp::OzOperand ozR, ozUV, ozVU;          // the localised update of the standard form
   // localised update: the B whose factorisation the last update call left (and its n, gen)
   const void* upd_B = nullptr;
@@ -646,11 +647,28 @@ gevp_status ensure_pipeline(gevp_ctx* h) {
 // Li = L^-1 D with D W D + sh I = L L^H (one cluster launch, *info set on a non-positive
 // pivot), dst = src Li^H = src D L^-H. False if the cluster factorisation is not available
 // for this order (nothing enqueued after the Gram matrix then).
+// The product runs emulated on the tensor cores when the solve's products are (its digit
+// operands in the block region of the main-stream scratch, free between the filter and the
+// Rayleigh-Ritz rotation), else on the FP64 pipe.
 bool cholqr_pass(gevp_ctx* h, int64_t n, int ma, const double2* src, int64_t lds, double2* dst, int64_t ldd, double sh,
                  int* info) {
   if (ma > cholinv_max_order()) return false;
   zgram(n, ma, ma, src, lds, src, lds, h->Gw, ma, 1, h->split, h->split_elems, h->gcnt, h->stream);
   if (!cholinv_small(ma, h->Gw, ma, sh, h->Gwi, ma, nullptr, 0, info, h->stream)) return false;
+  const int S = h->oz_slices;
+  if (S > 0 && h->ozmem[0] && h->ozmem_bytes[0] >= oz_main_bytes(n, S) &&
+      gevp::oz_operand_bytes((int)n, ma, S, 2) + gevp::oz_operand_bytes(ma, ma, S, 3) <=
+          gevp::oz_operand_bytes((int)n, (int)n, S, 3)) {
+    // dst = Y (L^-1 D)^H: the columns of (L^-1 D)^H are the conjugated rows of the lower L^-1 D
+    char* mem = oz_region(h, n, 2);
+    if (gevp::oz_split(h->ozY, mem, (int)n, ma, src, lds, 0, 0, S, 2, h->ozflags + 1, h->stream) == cudaSuccess &&
+        gevp::oz_split(h->ozLiH, mem + gevp::oz_operand_bytes((int)n, ma, S, 2), ma, ma, h->Gwi, ma, 1, 2, S, 3,
+                       h->ozflags + 1, h->stream) == cudaSuccess &&
+        gevp::oz_gemm(h->ozY, h->ozLiH, 0, 2, dst, ldd, h->ozflags, h->stream, nullptr, h->ozws, h->ozws_doubles) ==
+            cudaSuccess)
+      return true;
+    cudaGetLastError();
+  }
   ZgemmArgs q = zg((int)n, ma, ma, src, lds, 0, h->Gwi, ma, 1, dst, ldd);
   q.triB = 2;
   zgemm(q, h->split, h->split_elems, h->stream);

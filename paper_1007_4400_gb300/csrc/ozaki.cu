@@ -28,7 +28,9 @@
 // the MMAs of one unit (digit pair, K chunk) into one of two TMEM accumulators (128
 // columns each) while warps 0-7 drain the other: each thread owns one row and 64 columns,
 // converts the exact FP32 sums to integers and adds them up per level; at the end of a
-// level the FP64 Horner state, kept in the upper 256 TMEM columns, is updated. A grid that
+// level the FP64 Horner state, kept in the upper 256 TMEM columns, is updated. When a
+// tile's K range is short (S K <= 2048: the thin products with K = m), all pairs of a
+// level accumulate in one buffer, still exactly, and are drained once per level. A grid that
 // would leave SMs idle (a short M or N) cuts K into slices whose FP64 partials a second
 // kernel sums in slice order; a device flag can make a launch a no-op (a converged batch
 // problem inside a captured graph). All waits are bounded; on expiry the kernel records an
@@ -105,6 +107,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   const int nchunk = (klen + OZ_KCHUNK - 1) / OZ_KCHUNK;
   const int npairs = p.S * (p.S + 1) / 2;
   const int nunits = npairs * nchunk;
+  // A short K range (the thin products, K = m): all digit pairs of one level accumulate in
+  // the same TMEM buffer and are drained once per level instead of once per pair. Exact
+  // while a level's sum stays an FP32 integer: at most S pairs x 2 klen real products of
+  // at most 2^12 each, S klen <= 2048.
+  const bool grouped = nchunk == 1 && p.S * klen <= 2048;
   auto chunk_blocks = [&](int c) {   // 64-blocks of chunk c (one part of the embedding)
     const int a = klo + c * OZ_KCHUNK;
     return (min(khi, a + OZ_KCHUNK) - a) / OZ_TK;
@@ -170,11 +177,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     for (int i = max(0, it - OZ_ST); i < it; ++i) mbar_wait(&full[i % OZ_ST], (uint32_t)(i / OZ_ST) & 1u, p.err, 25);
   } else if (warp == OZ_EPI_WARPS + 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16(OZ_TM, OZ_TN);
-    int it = 0;
+    int it = 0, grp = 0;   // accumulation groups: the units, or the levels when grouped
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
-      const int buf = u & 1;
-      if (u >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((u >> 1) - 1) & 1u, p.err, 22)) break;
+      const int pi = u / nchunk;
+      const bool gs = !grouped || pair_s[pi] == 1, ge = !grouped || pair_last[pi];
+      const int buf = grp & 1;
+      if (gs && grp >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((grp >> 1) - 1) & 1u, p.err, 22)) break;
       fence_after();
       const uint32_t dt = tmem + (uint32_t)(buf * OZ_TN);
       const int nb2 = 2 * chunk_blocks(u % nchunk);
@@ -190,12 +199,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
         for (int kk = 0; kk < OZ_TK / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;
-          umma(dt, da + off, db + off, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          umma(dt, da + off, db + off, idesc, (i > 0 || kk > 0 || !gs) ? 1u : 0u);
         }
         umma_commit(&empty[st]);
       }
       if (!ok) break;
-      umma_commit(&tfull[buf]);
+      if (ge) {
+        umma_commit(&tfull[buf]);
+        ++grp;
+      }
     }
   } else if (warp < OZ_EPI_WARPS) {
     const int q = warp & 3, ch = warp >> 2;
@@ -213,10 +225,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc[j] = 0;
     bool first_level = true, ok = true;
+    int grp = 0;
     for (int u = 0; u < nunits; ++u) {
-      const int buf = u & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(u >> 1) & 1u, p.err, 24) ? 1 : 0) != 0;
+      // (grouped: the buffer holds a level's running sum until its last pair)
+      if (grouped && !pair_last[u / nchunk]) continue;
+      const int buf = grp & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(grp >> 1) & 1u, p.err, 24) ? 1 : 0) != 0;
       if (!ok) break;
+      ++grp;
       fence_after();
 #pragma unroll
       for (int g = 0; g < 4; ++g) {

@@ -33,7 +33,11 @@ def bound(K, S):
     return 16 * 2 * K * (S + 3) * 2.0 ** (-7 * S - 2)
 
 
-@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 70, 64), (257, 300, 1000), (128, 129, 2100), (64, 200, 4177)])
+# (2048, 140, 140): the solver's thin products (K = m), whose digit pairs of one level
+# accumulate in one tensor-memory buffer; (257, 300, 1000) also takes that form per split-K
+# slice (K slices of 128); the last two keep one buffer per pair
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 70, 64), (2048, 140, 140), (257, 300, 1000), (128, 129, 2100),
+                                   (64, 200, 4177)])
 @pytest.mark.parametrize("S", [1, 3, 8])
 def test_exact_on_small_integers(cuda, M, N, K, S):
     # entries in {-2..2} + i{-2..2}: one digit holds them, every product and sum is exact
@@ -45,7 +49,7 @@ def test_exact_on_small_integers(cuda, M, N, K, S):
     assert np.array_equal(D, A @ B.conj().T)
 
 
-@pytest.mark.parametrize("M,N,K", [(200, 130, 700), (129, 257, 2048), (300, 64, 2049), (96, 96, 5000)])
+@pytest.mark.parametrize("M,N,K", [(200, 130, 700), (4096, 140, 140), (129, 257, 2048), (300, 64, 2049), (96, 96, 5000)])
 def test_random_within_bound(cuda, M, N, K):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(2000 + M + N + K)
