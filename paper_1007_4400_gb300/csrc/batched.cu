@@ -743,25 +743,9 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
   enum { EV_T0 = 2, EV_CHOL, EV_RED, EV_BND, EV_RND0, EV_RND1, EV_FIN0, EV_FIN1, EV_F0, EV_F1, EV_END };
   BCK(cudaEventRecord(evt(P, EV_T0), s));
 
-  // ---- Cholesky of every B_k (sequence-invariant)
-  BCK(cudaMemsetAsync(P->dInfo, 0, np * sizeof(int), s));
-  for (int k = 0; k < np; ++k) {
-    BDesc& d = P->hD[k];
-    zcopy2d(n[k], n[k], (const double2*)B[k], ldb[k], d.L, n[k], s);
-    potrf_lower(n[k], d.L, n[k], P->dInfo + k, d.Linv, n[k], s);
-    trtri_lower(n[k], d.L, n[k], d.Linv, n[k], P->trtri_ws, P->trtri_elems, s, true);
-  }
-  BCK(cudaMemcpyAsync(P->hInfo, P->dInfo, np * sizeof(int), cudaMemcpyDeviceToHost, s));
-  BCK(cudaEventRecord(evt(P, EV_CHOL), s));
-  BCK(cudaStreamSynchronize(s));
-  for (int k = 0; k < np; ++k)
-    if (P->hInfo[k] != 0) {
-      char buf[96];
-      snprintf(buf, sizeof buf, "B of k-point %d is not positive definite (pivot %d)", k, P->hInfo[k]);
-      ctx_set_error(h, buf);
-      return GEVP_ERR_NOT_HPD;
-    }
-  // digit forms of L^-1 for the emulated reduction (o.reduce_slices digits per entry)
+  // digit memory of the emulated products (o.reduce_slices digits per entry): the L^-1
+  // operands of every k-point and a scratch pair; the factorisations below use the front
+  // of it before the L^-1 operands are split there
   P->oz_S = P->nmax <= 30720 ? P->oz_key : 0;
   if (P->oz_S > 0) {
     const int S = P->oz_S;
@@ -781,6 +765,47 @@ extern "C" gevp_status gevp_solve_batched(gevp_handle h, int nk, int nsteps, con
     }
     P->oz_flags = (int*)P->oz_mem;
     BCK(cudaMemsetAsync(P->oz_flags, 0, 2 * sizeof(int), s));
+  }
+
+  // ---- Cholesky of every B_k (sequence-invariant): recursive with emulated off-diagonal
+  // products when the products are emulated, else blocked on the FP64 pipe
+  BCK(cudaMemsetAsync(P->dInfo, 0, np * sizeof(int), s));
+  for (int k = 0; k < np; ++k) {
+    BDesc& d = P->hD[k];
+    zcopy2d(n[k], n[k], (const double2*)B[k], ldb[k], d.L, n[k], s);
+    cudaError_t ce = cudaErrorNotSupported;
+    if (P->oz_S > 0) {
+      CholRes r{};
+      r.memA = P->oz_mem + 256;
+      r.memB = r.memA + oz_operand_bytes((int)n[k], (int)n[k], P->oz_S, 2);
+      r.T = d.T;
+      r.ldt = n[k];
+      r.ws = P->oz_ws;
+      r.ws_doubles = P->oz_ws_doubles;
+      r.flags = P->oz_flags;
+      r.info = P->dInfo + k;
+      r.S = P->oz_S;
+      r.s = s;
+      ce = chol_recursive(n[k], d.L, n[k], d.Linv, n[k], r);
+      if (ce != cudaSuccess && ce != cudaErrorNotSupported) return fail(ce, "chol_recursive");
+    }
+    if (ce == cudaErrorNotSupported) {
+      potrf_lower(n[k], d.L, n[k], P->dInfo + k, d.Linv, n[k], s);
+      trtri_lower(n[k], d.L, n[k], d.Linv, n[k], P->trtri_ws, P->trtri_elems, s, true);
+    }
+  }
+  BCK(cudaMemcpyAsync(P->hInfo, P->dInfo, np * sizeof(int), cudaMemcpyDeviceToHost, s));
+  BCK(cudaEventRecord(evt(P, EV_CHOL), s));
+  BCK(cudaStreamSynchronize(s));
+  for (int k = 0; k < np; ++k)
+    if (P->hInfo[k] != 0) {
+      char buf[96];
+      snprintf(buf, sizeof buf, "B of k-point %d is not positive definite (pivot %d)", k, P->hInfo[k]);
+      ctx_set_error(h, buf);
+      return GEVP_ERR_NOT_HPD;
+    }
+  if (P->oz_S > 0) {
+    const int S = P->oz_S;
     char* q = P->oz_mem + 256;
     P->ozLA.assign(np, OzOperand{});
     P->ozLB.assign(np, OzOperand{});

@@ -340,6 +340,75 @@ bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* 
   return cholinv_launch<8>(m, W, ldw, shift, Li, ldi, Lf, ldl, info, info_base, s);
 }
 
+namespace {
+
+// The recursion of chol_recursive: a block of order n splits as n1 + n2 (n1 a multiple of
+// 128 near n / 2):
+//   [A11 .  ]   [L11  .  ] [L11^H L21^H]
+//   [A21 A22] = [L21 L22 ] [  .   L22^H],   L21 = A21 L11^-H,  A22 - L21 L21^H = L22 L22^H,
+//   (L^-1)21 = -L22^-1 L21 L11^-1,
+// the four off-diagonal products emulated, leaves of order <= kCholLeaf factored and
+// inverted in one cluster launch each.
+struct CholRec {
+  const CholRes& r;
+  cudaError_t err = cudaSuccess;
+
+  bool product(OzOperand& a, OzOperand& b, int triA, int triB, double2* D, int64_t ldd) {
+    const bool ws = r.ws && oz_split_k_doubles(a.rows, b.rows) <= r.ws_doubles;
+    err = oz_gemm(a, b, triA, triB, D, ldd, r.flags, r.s, nullptr, ws ? r.ws : nullptr, ws ? r.ws_doubles : 0);
+    return err == cudaSuccess;
+  }
+  bool split(OzOperand& op, bool roleA, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
+             bool cols) {
+    err = oz_split(op, roleA ? r.memA : r.memB, rows, K, X, ldx, conj, mask, r.S, roleA ? 2 : 3, r.flags + 1, r.s,
+                   cols);
+    return err == cudaSuccess;
+  }
+  // false with err == cudaSuccess: a leaf could not be launched (nothing enqueued if k0 == 0)
+  bool run(int64_t n, double2* A, int64_t lda, double2* Li, int64_t ldi, int64_t k0) {
+    if (n <= kCholLeaf) return cholinv_small((int)n, A, lda, 0.0, Li, ldi, A, lda, r.info, r.s, (int)k0);
+    const int64_t n1 = std::max<int64_t>(128, (n / 2) / 128 * 128), n2 = n - n1;
+    double2 *A21 = A + n1 * lda, *A22 = A21 + n1, *Li21 = Li + n1 * ldi, *Li22 = Li21 + n1;
+    OzOperand a, b;
+    const int i1 = (int)n1, i2 = (int)n2;
+    if (!run(n1, A, lda, Li, ldi, k0)) return false;
+    // L21 = A21 L11^-H: the columns of L11^-H are the conjugated rows of L11^-1 (k <= j)
+    if (!split(a, true, i2, i1, A21, lda, 0, 0, false) || !split(b, false, i1, i1, Li, ldi, 1, 2, false) ||
+        !product(a, b, 0, 2, A21, lda))
+      return false;
+    // A22 -= L21 L21^H (lower triangle), the product through the scratch T
+    if (!split(a, true, i2, i1, A21, lda, 0, 0, false) || !split(b, false, i2, i1, A21, lda, 1, 0, false) ||
+        !product(a, b, 0, 0, r.T, r.ldt))
+      return false;
+    zsub_lower(n2, A22, lda, r.T, r.ldt, r.s);
+    if (!run(n2, A22, lda, Li22, ldi, k0 + n1)) {
+      if (err == cudaSuccess) err = cudaErrorLaunchFailure;   // the first leaf launched: this one should too
+      return false;
+    }
+    // T = L21 L11^-1 (the columns of the lower L11^-1 from their diagonal down), then
+    // (L^-1)21 = -L22^-1 T
+    if (!split(a, true, i2, i1, A21, lda, 0, 0, false) || !split(b, false, i1, i1, Li, ldi, 0, 3, true) ||
+        !product(a, b, 0, 1, r.T, r.ldt))
+      return false;
+    if (!split(a, true, i2, i2, Li22, ldi, 0, 2, false) || !split(b, false, i1, i2, r.T, r.ldt, 0, 0, true) ||
+        !product(a, b, 1, 0, Li21, ldi))
+      return false;
+    zneg(n2, n1, Li21, ldi, r.s);
+    return true;
+  }
+};
+
+}  // namespace
+
+cudaError_t chol_recursive(int64_t n, double2* A, int64_t lda, double2* Li, int64_t ldi, const CholRes& r) {
+  if (n < 1 || cholinv_max_order() < kCholLeaf) return cudaErrorNotSupported;
+  if (n > kCholLeaf) zero_upper(n, Li, ldi, r.s);   // the leaves and products fill the lower part
+  CholRec rec{r};
+  if (!rec.run(n, A, lda, Li, ldi, 0)) return rec.err == cudaSuccess ? cudaErrorNotSupported : rec.err;
+  if (n > kCholLeaf) zero_upper(n, A, lda, r.s);
+  return cudaSuccess;
+}
+
 size_t zgram_counters() { return 4096; }
 
 void zgram(int64_t n, int mx, int my, const double2* X, int64_t ldx, const double2* Y, int64_t ldy, double2* G,

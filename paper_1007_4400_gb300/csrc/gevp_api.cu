@@ -434,87 +434,16 @@ gevp_status oz_times_block(gevp_ctx* h, const gevp::OzOperand& M, int64_t n, int
   return GEVP_OK;
 }
 
-// Recursive Cholesky factorisation with the inverse, for the emulated-product mode. On
-// this part one SM retires about two FP64 FMAs per clock: the blocked right-looking form
-// (potrf.cu) spends its time in rank-32 FP64 updates and a chain of one-CTA diagonal
-// blocks. Here a block of order n splits as n1 + n2 (n1 a multiple of 128 near n / 2):
-//   [A11 .  ]   [L11  .  ] [L11^H L21^H]
-//   [A21 A22] = [L21 L22 ] [  .   L22^H],   L21 = A21 L11^-H,  A22 - L21 L21^H = L22 L22^H,
-//   (L^-1)21 = -L22^-1 L21 L11^-1,
-// the four off-diagonal products run on the tensor cores (emulated FP64), and leaves of
-// order <= kCholLeaf are factored and inverted in one cluster launch each (cholqr.cu).
-// L (upper triangle zeroed) replaces the matrix in A; Li receives L^-1. A non-positive
-// pivot of a leaf sets *h->info to its global 1-based index; the later launches then run
-// on stale blocks and their results are discarded by the caller.
-constexpr int64_t kCholLeaf = 256;
-
-struct CholRec {
-  gevp_ctx* h;
-  int64_t ntop;   // order of the whole matrix: the digit regions are laid out for it
-  int S;
-  gevp_status st = GEVP_OK;
-
-  bool product(gevp::OzOperand& a, gevp::OzOperand& b, int triA, int triB, double2* D, int64_t ldd) {
-    const bool ws = gevp::oz_split_k_doubles(a.rows, b.rows) <= h->ozws_doubles;
-    if (gevp::oz_gemm(a, b, triA, triB, D, ldd, h->ozflags, h->stream, nullptr, ws ? h->ozws : nullptr,
-                      ws ? h->ozws_doubles : 0) != cudaSuccess) {
-      st = GEVP_ERR_CUDA;
-      return false;
-    }
-    return true;
-  }
-  bool split(gevp::OzOperand& op, int which, int rows, int K, const double2* X, int64_t ldx, int conj, int mask,
-             int npl, bool cols) {
-    if (gevp::oz_split(op, oz_region(h, ntop, which), rows, K, X, ldx, conj, mask, S, npl, h->ozflags + 1, h->stream,
-                       cols) != cudaSuccess) {
-      st = GEVP_ERR_CUDA;
-      return false;
-    }
-    return true;
-  }
-  // false with st == GEVP_OK: a leaf could not be launched (nothing enqueued if k0 == 0)
-  bool run(int64_t n, double2* A, int64_t lda, double2* Li, int64_t ldi, int64_t k0) {
-    if (n <= kCholLeaf)
-      return cholinv_small((int)n, A, lda, 0.0, Li, ldi, A, lda, h->info, h->stream, (int)k0);
-    const int64_t n1 = std::max<int64_t>(128, (n / 2) / 128 * 128), n2 = n - n1;
-    double2 *A21 = A + n1 * lda, *A22 = A21 + n1, *Li21 = Li + n1 * ldi, *Li22 = Li21 + n1;
-    gevp::OzOperand a, b;
-    const int i1 = (int)n1, i2 = (int)n2;
-    if (!run(n1, A, lda, Li, ldi, k0)) return false;
-    // L21 = A21 L11^-H: the columns of L11^-H are the conjugated rows of L11^-1 (k <= j)
-    if (!split(a, 0, i2, i1, A21, lda, 0, 0, 2, false) || !split(b, 1, i1, i1, Li, ldi, 1, 2, 3, false) ||
-        !product(a, b, 0, 2, A21, lda))
-      return false;
-    // A22 -= L21 L21^H (lower triangle), the product through the scratch T
-    if (!split(a, 0, i2, i1, A21, lda, 0, 0, 2, false) || !split(b, 1, i2, i1, A21, lda, 1, 0, 3, false) ||
-        !product(a, b, 0, 0, h->T, ntop))
-      return false;
-    zsub_lower(n2, A22, lda, h->T, ntop, h->stream);
-    if (!run(n2, A22, lda, Li22, ldi, k0 + n1)) {
-      if (st == GEVP_OK) st = GEVP_ERR_CUDA;   // the first leaf launched: this one should too
-      return false;
-    }
-    // T = L21 L11^-1 (the columns of the lower L11^-1 from their diagonal down), then
-    // (L^-1)21 = -L22^-1 T
-    if (!split(a, 0, i2, i1, A21, lda, 0, 0, 2, false) || !split(b, 1, i1, i1, Li, ldi, 0, 3, 3, true) ||
-        !product(a, b, 0, 1, h->T, ntop))
-      return false;
-    if (!split(a, 0, i2, i2, Li22, ldi, 0, 2, 2, false) || !split(b, 1, i1, i2, h->T, ntop, 0, 0, 3, true) ||
-        !product(a, b, 1, 0, Li21, ldi))
-      return false;
-    zneg(n2, n1, Li21, ldi, h->stream);
-    return true;
-  }
-};
-
-// h->L (holding B) -> L, h->Linv -> L^-1 by CholRec. false: not done (order above the
-// emulated products' limit, or the cluster leaves not launchable: nothing was enqueued;
-// *st set on a failure after work was enqueued).
+// h->L (holding B) -> L, h->Linv -> L^-1 by chol_recursive (cholqr.cu), its digit operands
+// in the first two regions of the main-stream scratch (the L^-1 digits, remade after it).
+// false: not done (order above the emulated products' limit, or the cluster leaves not
+// launchable: nothing was enqueued; *st set on a failure after work was enqueued).
 bool factor_emulated(gevp_ctx* h, int64_t n, gevp_status* st) {
   *st = GEVP_OK;
-  if (n > 30720 || cholinv_max_order() < kCholLeaf) return false;
+  if (n > 30720) return false;
   const int S = h->oz_slices;
-  if (n > kCholLeaf) {
+  gevp::CholRes r{};
+  if (n > gevp::kCholLeaf) {
     if ((*st = oz_reserve(h, 0, oz_main_bytes(n, S))) != GEVP_OK) return false;
     // split-K partials for the products near the leaves (up to 512 x 512 at 4 slices)
     const size_t wd = gevp::oz_split_k_doubles(512, 512) / 2;
@@ -533,14 +462,23 @@ bool factor_emulated(gevp_ctx* h, int64_t n, gevp_status* st) {
       h->ozws = (double*)p;
       h->ozws_doubles = wd;
     }
-    zero_upper(n, h->Linv, n, h->stream);
+    r.memA = oz_region(h, n, 0);
+    r.memB = oz_region(h, n, 1);
+    r.T = h->T;
+    r.ldt = n;
+    r.ws = h->ozws;
+    r.ws_doubles = h->ozws_doubles;
   }
-  CholRec r{h, n, S};
-  if (!r.run(n, h->L, n, h->Linv, n, 0)) {
-    *st = r.st;
+  r.flags = h->ozflags;
+  r.info = h->info;
+  r.S = S;
+  r.s = h->stream;
+  const cudaError_t e = gevp::chol_recursive(n, h->L, n, h->Linv, n, r);
+  if (e == cudaErrorNotSupported) return false;
+  if (e != cudaSuccess) {
+    *st = GEVP_ERR_CUDA;
     return false;
   }
-  if (n > kCholLeaf) zero_upper(n, h->L, n, h->stream);
   return true;
 }
 

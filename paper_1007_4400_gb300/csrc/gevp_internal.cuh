@@ -182,6 +182,34 @@ void zgram(int64_t n, int mx, int my, const double2* X, int64_t ldx, const doubl
 int cholinv_max_order();
 bool cholinv_small(int m, const double2* W, int64_t ldw, double shift, double2* Li, int64_t ldi, double2* Lf,
                    int64_t ldl, int* info, cudaStream_t s, int info_base = 0);
+// Recursive Cholesky factorisation with the inverse, for the emulated-product mode: A
+// (n x n, lower triangle read) -> L in place (upper triangle zeroed), Li <- L^-1. A block of
+// order n > kCholLeaf splits as n1 + n2 (n1 a multiple of 128 near n / 2) with
+// L21 = A21 L11^-H, L22 L22^H = A22 - L21 L21^H, (L^-1)21 = -L22^-1 L21 L11^-1 as emulated
+// products; leaves of order <= kCholLeaf are factored and inverted by cholinv_small.
+// Resources (CholRes): digit memory for one operand of up to n x n in the A role (memA,
+// oz_operand_bytes(n, n, S, 2)) and one in the B role (memB, npl 3), an n x n scratch T
+// (ld ldt), optional split-K partials, the products' status words (flags[0] error code,
+// flags[1] non-finite entry), the pivot word and the stream (memA, memB, T unused for
+// n <= kCholLeaf). Returns cudaSuccess when enqueued; cudaErrorNotSupported when nothing
+// was enqueued (no cluster launch possible); another error after work was enqueued. A
+// non-positive pivot sets *info to its global 1-based index (atomicCAS from 0); the later
+// launches then run on stale blocks and the results are to be discarded, the status
+// words possibly set by them with them.
+constexpr int64_t kCholLeaf = 256;
+struct CholRes {
+  char* memA;
+  char* memB;
+  double2* T;
+  int64_t ldt;
+  double* ws;
+  size_t ws_doubles;
+  int* flags;
+  int* info;
+  int S;
+  cudaStream_t s;
+};
+cudaError_t chol_recursive(int64_t n, double2* A, int64_t lda, double2* Li, int64_t ldi, const CholRes& r);
 
 // ---------------------------------------------------------------- backward
 // GA = gE X X^H, GB = -gE X diag(lam) X^H (lower tiles by GEMM, then Hermitian completion
