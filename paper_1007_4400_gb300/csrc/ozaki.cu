@@ -48,15 +48,17 @@ namespace gevp {
 namespace {
 
 constexpr int OZ_TM = 128;
-constexpr int OZ_TN = 128;
+constexpr int OZ_TN = 128;   // the usual tile width (a wider one serves 129..144 columns)
 constexpr int OZ_TK = 64;
 constexpr int OZ_ST = 6;
 constexpr int OZ_KCHUNK = 2048;
 constexpr int OZ_EPI_WARPS = 8;
 constexpr int OZ_THREADS = (OZ_EPI_WARPS + 2) * 32;
 constexpr int OZ_MAXPAIRS = kOzSlicesMax * (kOzSlicesMax + 1) / 2;
-constexpr uint32_t OZ_TILE_BYTES = OZ_TM * OZ_TK * 2;   // one 128 x 64 BF16 box (A and B alike)
-constexpr size_t OZ_SMEM = (size_t)OZ_ST * 2 * OZ_TILE_BYTES + 1024;
+constexpr uint32_t OZ_A_BYTES = OZ_TM * OZ_TK * 2;   // one 128 x 64 BF16 box of A
+// a stage: the A box and a TN x 64 box of B (both multiples of the 1024-byte swizzle atom)
+__host__ __device__ constexpr uint32_t oz_stage_bytes(int TN) { return OZ_A_BYTES + (uint32_t)TN * OZ_TK * 2; }
+constexpr size_t oz_smem(int TN) { return (size_t)OZ_ST * oz_stage_bytes(TN) + 1024; }
 
 struct OzMaps {
   CUtensorMap a[2];   // op(A) digit planes: re, im
@@ -80,7 +82,14 @@ struct OzParams {
   int kspan;           // split K: the K range of one slice (a multiple of 64)
 };
 
+// TN: tile width (128, or 144 for 129..144 columns in one tile); NBUF: TMEM accumulator
+// buffers (two of TN columns with the Horner state of TN values in the upper 256 columns;
+// one for TN = 144, whose Horner state takes 288 columns)
+template <int TN, int NBUF>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
+  static_assert(NBUF * TN + 2 * TN <= 512, "TMEM: accumulators and Horner state exceed 512 columns");
+  constexpr int CPT = TN / 2;   // columns of one epilogue thread
+  constexpr uint32_t STAGE = oz_stage_bytes(TN);
   if (p.active && *p.active == 0) return;   // uniform: before any barrier or TMEM allocation
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[OZ_ST], empty[OZ_ST], tfull[2], tempty[2];
@@ -92,13 +101,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   // they read the same B tiles (first half of the embedding's K) while both are in L2
   const int part = blockIdx.y & 1;   // 0: real part of D, 1: imaginary part
   const int m0 = (blockIdx.y >> 1) * OZ_TM;
-  const int n0 = blockIdx.x * OZ_TN;
+  const int n0 = blockIdx.x * TN;
   // K range of the tile from the triangular structure, in whole 64-blocks
   int klo = 0, khi = p.k_pad;
   if (p.triA == 1) khi = min(khi, m0 + OZ_TM);
   if (p.triA == 2) klo = max(klo, m0);
   if (p.triB == 1) klo = max(klo, n0);
-  if (p.triB == 2) khi = min(khi, n0 + OZ_TN);
+  // (whole 64-blocks: n0 + TN is not a multiple of 64 for TN = 144, and the K entries past
+  // the triangle up to the next block boundary are zero digits of the masked operand)
+  if (p.triB == 2) khi = min(khi, (n0 + TN + OZ_TK - 1) / OZ_TK * OZ_TK);
   if (p.ws) {   // split K: this CTA's slice
     klo = max(klo, (int)blockIdx.z * p.kspan);
     khi = min(khi, ((int)blockIdx.z + 1) * p.kspan);
@@ -165,10 +176,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         const int kh = i / nb, kx = kbase + (i % nb) * OZ_TK;
         const int pa = part ^ kh;
         const int pb = kh == 0 ? 0 : (part == 0 ? 2 : 1);
-        uint8_t* sa_tile = smem + (size_t)st * 2 * OZ_TILE_BYTES;
-        mbar_expect_tx(&full[st], 2 * OZ_TILE_BYTES);
+        uint8_t* sa_tile = smem + (size_t)st * STAGE;
+        mbar_expect_tx(&full[st], STAGE);
         tma_load_3d(sa_tile, &maps.a[pa], kx, m0, sa, &full[st]);
-        tma_load_3d(sa_tile + OZ_TILE_BYTES, &maps.b[pb], kx, n0, tb, &full[st]);
+        tma_load_3d(sa_tile + OZ_A_BYTES, &maps.b[pb], kx, n0, tb, &full[st]);
       }
     }
     // every copy issued has landed before the CTA leaves (normally they were all consumed;
@@ -176,16 +187,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     // last issue of every stage
     for (int i = max(0, it - OZ_ST); i < it; ++i) mbar_wait(&full[i % OZ_ST], (uint32_t)(i / OZ_ST) & 1u, p.err, 25);
   } else if (warp == OZ_EPI_WARPS + 1 && lane == 0) {
-    const uint32_t idesc = idesc_bf16(OZ_TM, OZ_TN);
+    const uint32_t idesc = idesc_bf16(OZ_TM, TN);
     int it = 0, grp = 0;   // accumulation groups: the units, or the levels when grouped
     bool ok = true;
     for (int u = 0; u < nunits && ok; ++u) {
       const int pi = u / nchunk;
       const bool gs = !grouped || pair_s[pi] == 1, ge = !grouped || pair_last[pi];
-      const int buf = grp & 1;
-      if (gs && grp >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((grp >> 1) - 1) & 1u, p.err, 22)) break;
+      const int buf = grp % NBUF;
+      if (gs && grp >= NBUF && !mbar_wait(&tempty[buf], (uint32_t)((grp / NBUF) - 1) & 1u, p.err, 22)) break;
       fence_after();
-      const uint32_t dt = tmem + (uint32_t)(buf * OZ_TN);
+      const uint32_t dt = tmem + (uint32_t)(buf * TN);
       const int nb2 = 2 * chunk_blocks(u % nchunk);
       for (int i = 0; i < nb2; ++i, ++it) {
         const int st = it % OZ_ST;
@@ -194,8 +205,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
           break;
         }
         fence_after();
-        const uint8_t* base = smem + (size_t)st * 2 * OZ_TILE_BYTES;
-        const uint64_t da = sdesc(su32(base)), db = sdesc(su32(base + OZ_TILE_BYTES));
+        const uint8_t* base = smem + (size_t)st * STAGE;
+        const uint64_t da = sdesc(su32(base)), db = sdesc(su32(base + OZ_A_BYTES));
 #pragma unroll
         for (int kk = 0; kk < OZ_TK / 16; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;
@@ -212,8 +223,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   } else if (warp < OZ_EPI_WARPS) {
     const int q = warp & 3, ch = warp >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const uint32_t col0 = (uint32_t)(ch * 64);
-    const uint32_t hcol = 256u + 2u * col0;   // FP64 Horner state: 2 TMEM columns per value
+    const uint32_t col0 = (uint32_t)(ch * CPT);
+    const uint32_t hcol = (uint32_t)(NBUF * TN) + 2u * col0;   // FP64 Horner state: 2 TMEM columns per value
     const int row = m0 + q * 32 + lane;
     const bool row_ok = row < p.M;
     const int er = row_ok ? p.ea[row] : 0;
@@ -221,26 +232,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     // partial (double row N + col of plane (z, part) of the workspace)
     double* Dd = p.ws ? p.ws + ((size_t)blockIdx.z * 2 + part) * (size_t)p.M * p.N : (double*)p.D;
     const int64_t ostr = p.ws ? 1 : 2, opart = p.ws ? 0 : part, old = p.ws ? p.N : p.ldd;
-    int acc[64];
+    int acc[CPT];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    for (int j = 0; j < CPT; ++j) acc[j] = 0;
     bool first_level = true, ok = true;
     int grp = 0;
     for (int u = 0; u < nunits; ++u) {
       // (grouped: the buffer holds a level's running sum until its last pair)
       if (grouped && !pair_last[u / nchunk]) continue;
-      const int buf = grp & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(grp >> 1) & 1u, p.err, 24) ? 1 : 0) != 0;
+      const int buf = grp % NBUF;
+      ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], (uint32_t)(grp / NBUF) & 1u, p.err, 24) ? 1 : 0) != 0;
       if (!ok) break;
       ++grp;
       fence_after();
+      // (CPT = 72: the fifth load's last 8 columns are not this thread's and are ignored)
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < (CPT + 15) / 16; ++g) {
         uint32_t r[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)(buf * OZ_TN) + col0 + 16u * g, r);
+        tmem_ld16(tmem + lane_base + (uint32_t)(buf * TN) + col0 + 16u * g, r);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[16 * g + j] += __float2int_rn(__uint_as_float(r[j]));
+        for (int j = 0; j < 16; ++j)
+          if (16 * g + j < CPT) acc[16 * g + j] += __float2int_rn(__uint_as_float(r[j]));
       }
       fence_before();
       __syncwarp();
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       // end of a level: h <- h 2^-7 + I_L (FP64), kept in TMEM until the last level
       const bool last_level = (pi == npairs - 1);
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
+      for (int g = 0; g < CPT / 8; ++g) {
         uint32_t hv[16];
         if (!first_level) {
           tmem_ld16(tmem + lane_base + hcol + 16u * g, hv);
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       first_level = false;
     }
     if (nunits == 0 && row_ok) {
-      for (int j = 0; j < 64; ++j) {
+      for (int j = 0; j < CPT; ++j) {
         const int col = n0 + (int)col0 + j;
         if (col < p.N) Dd[ostr * ((int64_t)row * old + col) + opart] = 0.0;
       }
@@ -519,13 +532,13 @@ EncodeTiledFn oz_encode() {
   return fn;
 }
 
-// 3D map over the digit planes of one part: (k, row, digit), box 64 x 128 x 1
-bool oz_map(CUtensorMap* map, void* base, int k_pad, int rows_pad, int S) {
+// 3D map over the digit planes of one part: (k, row, digit), box 64 x box_rows x 1
+bool oz_map(CUtensorMap* map, void* base, int k_pad, int rows_pad, int S, int box_rows) {
   EncodeTiledFn enc = oz_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)S};
   cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * k_pad * 2};
-  cuuint32_t box[3] = {OZ_TK, OZ_TM, 1};
+  cuuint32_t box[3] = {OZ_TK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -585,13 +598,18 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
   // the integer sums of one level hold at most S products of 2^24 per K chunk
   if (A.k_pad > 15 * OZ_KCHUNK) return cudaErrorInvalidValue;
   if (A.rows == 0 || B.rows == 0) return cudaSuccess;
+  // 129..144 columns (the Rayleigh-Ritz block W = C Q at m = 140) in one 144-wide tile with
+  // a single accumulator instead of a second 128-wide tile that is mostly padding (the
+  // operand's rows are padded to 256, so the 144-row box stays inside them)
+  const int tn = (B.rows > OZ_TN && B.rows <= 144) ? 144 : OZ_TN;
+  const int ntile = (B.rows + tn - 1) / tn;
   OzMaps maps;
   std::memset(&maps, 0, sizeof maps);
   const size_t pa = (size_t)A.S * A.rows_pad * A.k_pad, pb = (size_t)B.S * B.rows_pad * B.k_pad;
   for (int i = 0; i < 2; ++i)
-    if (!oz_map(&maps.a[i], A.planes + i * pa, A.k_pad, A.rows_pad, A.S)) return cudaErrorInvalidValue;
+    if (!oz_map(&maps.a[i], A.planes + i * pa, A.k_pad, A.rows_pad, A.S, OZ_TM)) return cudaErrorInvalidValue;
   for (int i = 0; i < 3; ++i)
-    if (!oz_map(&maps.b[i], B.planes + i * pb, B.k_pad, B.rows_pad, B.S)) return cudaErrorInvalidValue;
+    if (!oz_map(&maps.b[i], B.planes + i * pb, B.k_pad, B.rows_pad, B.S, tn)) return cudaErrorInvalidValue;
   OzParams p;
   p.M = A.rows;
   p.N = B.rows;
@@ -614,7 +632,7 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ctas = (B.rows_pad / OZ_TN) * 2 * p.mt;
+    const int ctas = ntile * 2 * p.mt;
     const int kb = p.k_pad / OZ_TK;
     int want = std::min(std::min(kOzSplitKMax, kb), sms / std::max(ctas, 1));
     if (want >= 2) {
@@ -626,27 +644,31 @@ cudaError_t oz_gemm(const OzOperand& A, const OzOperand& B, int triA, int triB, 
   }
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<OZ_TN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)oz_smem(OZ_TN));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(oz_gemm_kernel<144, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem(144));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(B.rows_pad / OZ_TN, 2 * p.mt, nz);
+  dim3 grid(ntile, 2 * p.mt, nz);
   void* kt0 = kt_enabled() ? kt_begin(s) : nullptr;
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(maps, p);
+  if (tn == 144) oz_gemm_kernel<144, 1><<<grid, OZ_THREADS, oz_smem(144), s>>>(maps, p);
+  else oz_gemm_kernel<OZ_TN, 2><<<grid, OZ_THREADS, oz_smem(OZ_TN), s>>>(maps, p);
   LAUNCH_NOTE(1);
   if (kt0) {
     // algorithmic: the complex product over the K ranges the tiles process (8 flop per
     // complex multiply-add); executed: the digit pairs' real products of the embedding
     double alg = 0.0;
     for (int mt = 0; mt < p.mt; ++mt)
-      for (int nt = 0; nt < B.rows_pad / OZ_TN; ++nt) {
-        const int m0 = mt * OZ_TM, n0 = nt * OZ_TN;
+      for (int nt = 0; nt < ntile; ++nt) {
+        const int m0 = mt * OZ_TM, n0 = nt * tn;
         int klo = 0, khi = p.k_pad;
         if (triA == 1) khi = std::min(khi, m0 + OZ_TM);
         if (triA == 2) klo = std::max(klo, m0);
         if (triB == 1) klo = std::max(klo, n0);
-        if (triB == 2) khi = std::min(khi, n0 + OZ_TN);
-        const int rows = std::min(OZ_TM, p.M - m0), cols = std::min(OZ_TN, p.N - n0);
+        if (triB == 2) khi = std::min(khi, (n0 + tn + OZ_TK - 1) / OZ_TK * OZ_TK);
+        const int rows = std::min(OZ_TM, p.M - m0), cols = std::min(tn, p.N - n0);
         if (khi > klo && rows > 0 && cols > 0) alg += 8.0 * rows * cols * (double)(khi - klo);
       }
     const double pairs = (double)p.S * (p.S + 1) / 2;

@@ -35,9 +35,11 @@ def bound(K, S):
 
 # (2048, 140, 140): the solver's thin products (K = m), whose digit pairs of one level
 # accumulate in one tensor-memory buffer; (257, 300, 1000) also takes that form per split-K
-# slice (K slices of 128); the last two keep one buffer per pair
+# slice (K slices of 128); the last two keep one buffer per pair. N from 129 to 144 runs
+# in one 144-wide tile with a single accumulator: (128, 129, 2100), (2048, 140, 140),
+# (300, 144, 2048), the solver's W = C Q shape
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (130, 70, 64), (2048, 140, 140), (257, 300, 1000), (128, 129, 2100),
-                                   (64, 200, 4177)])
+                                   (300, 144, 2048), (64, 200, 4177)])
 @pytest.mark.parametrize("S", [1, 3, 8])
 def test_exact_on_small_integers(cuda, M, N, K, S):
     # entries in {-2..2} + i{-2..2}: one digit holds them, every product and sum is exact
@@ -49,7 +51,8 @@ def test_exact_on_small_integers(cuda, M, N, K, S):
     assert np.array_equal(D, A @ B.conj().T)
 
 
-@pytest.mark.parametrize("M,N,K", [(200, 130, 700), (4096, 140, 140), (129, 257, 2048), (300, 64, 2049), (96, 96, 5000)])
+@pytest.mark.parametrize("M,N,K", [(200, 130, 700), (4096, 140, 140), (2048, 140, 2048), (129, 257, 2048),
+                                   (300, 64, 2049), (96, 96, 5000)])
 def test_random_within_bound(cuda, M, N, K):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(2000 + M + N + K)
@@ -107,7 +110,9 @@ def test_nan_is_an_error(cuda):
     assert e.value.status == 7
 
 
-@pytest.mark.parametrize("n", [1, 17, 200, 333])
+# 130 and 144: the right operands of the reduction's second product (L^-H, triangular)
+# have 129..144 rows and run in one 144-wide tile, whose triangle ends inside a K block
+@pytest.mark.parametrize("n", [1, 17, 130, 144, 200, 333])
 def test_reduce_emulated_vs_oracle(cuda, orc, n):
     from paper_1007_4400_gb300 import gevp
     rng = np.random.default_rng(4000 + n)
