@@ -33,8 +33,10 @@ def split(X, S):
     return e, digits(X.real), digits(X.imag)
 
 
-def emulate(A, B, S, kchunk=2048):
-    """A B^H through the scheme; also returns the largest |partial sum| seen in a unit."""
+def emulate(A, B, S, kchunk=2048, grouped=False):
+    """A B^H through the scheme; also returns the largest |partial sum| seen in a unit.
+    grouped: the pairs of one level share one running sum (the accumulator of a level, for
+    S K <= 2048), instead of one per pair."""
     ea, Ar, Ai = split(A, S)
     eb, Br, Bi = split(B.conj(), S)
     K = A.shape[1]
@@ -44,6 +46,7 @@ def emulate(A, B, S, kchunk=2048):
         h = None
         for L in range(S + 1, 1, -1):
             I = np.zeros((A.shape[0], B.shape[0]), dtype=np.int64)
+            run = np.zeros(I.shape, dtype=np.int64)
             for s in range(1, L):
                 t = L - s
                 for k0 in range(0, K, kchunk):
@@ -52,13 +55,18 @@ def emulate(A, B, S, kchunk=2048):
                         terms = [(Ar[s - 1][:, sl], Br[t - 1][:, sl]), (Ai[s - 1][:, sl], -Bi[t - 1][:, sl])]
                     else:
                         terms = [(Ai[s - 1][:, sl], Br[t - 1][:, sl]), (Ar[s - 1][:, sl], Bi[t - 1][:, sl])]
-                    # the running sum of a unit, term by term, in the order the MMA adds them
-                    run = np.zeros(I.shape, dtype=np.int64)
+                    # the running sum of a unit (or of the level), term by term, in the
+                    # order the MMA adds them
+                    if not grouped:
+                        run = np.zeros(I.shape, dtype=np.int64)
                     for X, Y in terms:
                         for kk in range(X.shape[1]):
                             run += np.outer(X[:, kk], Y[:, kk])
                             worst = max(worst, int(np.abs(run).max()))
-                    I += run
+                    if not grouped:
+                        I += run
+            if grouped:
+                I = run
             assert np.abs(I).max() < 2 ** 31   # the level sum fits the kernel's int32
             h = I.astype(float) if h is None else h * 2.0 ** -7 + I
         out.append(np.ldexp(h, ea[:, None] + eb[None, :] - 14))
@@ -113,3 +121,24 @@ def test_chunked_units_equal_one_pass_for_short_k():
     D1, _ = emulate(A, B, 8, kchunk=2048)
     D2, _ = emulate(A, B, 8, kchunk=64)
     assert np.array_equal(D1, D2)
+
+
+def test_level_grouped_accumulation_stays_exact():
+    # S K <= 2048: all digit pairs of a level accumulate in one FP32 buffer; S pairs of
+    # 2K real products of at most 2^12 stay within 2^24 (exact FP32 integers), including
+    # for the extreme-digit input, and give the same product as one running sum per pair
+    for S, K in ((8, 256), (4, 512), (3, 600)):
+        x = (0.5 - 2.0 ** -22) * np.ones(K)
+        A = (x + 1j * x)[None, :]
+        B = (x - 1j * x)[None, :]
+        Dg, worst = emulate(A, B, S, grouped=True)
+        assert worst <= 2 ** 24
+        Dp, _ = emulate(A, B, S)
+        assert np.array_equal(Dg, Dp)
+    rng = np.random.default_rng(63)
+    A = (rng.standard_normal((4, 256)) + 1j * rng.standard_normal((4, 256))) * np.exp(rng.uniform(-5, 5, (4, 1)))
+    B = rng.standard_normal((3, 256)) + 1j * rng.standard_normal((3, 256))
+    Dg, worst = emulate(A, B, 8, grouped=True)
+    assert worst <= 2 ** 24
+    assert np.array_equal(Dg, emulate(A, B, 8)[0])
+    assert np.all(np.abs(Dg - A @ B.conj().T) <= bound(A, B, 8) + 1e-300)
