@@ -23,7 +23,8 @@
 // 2K (S + 3) 2^(-7S - 2) in the worst case (K complex terms), the FP64 product's bound
 // K u sum_k |a_ik||b_kj| being of the same order for S = 8.
 //
-// GEMM kernel: one CTA per 128 x 128 tile of the real or the imaginary part of D. Warp 8
+// GEMM kernel: one CTA per 128 x 128 tile of the real or the imaginary part of D (128 x 144
+// for a D of 129..144 columns, with one accumulator, see oz_gemm_kernel). Warp 8
 // issues TMA loads (3D maps: k, row, digit; 128-byte swizzle; six stages), warp 9 issues
 // the MMAs of one unit (digit pair, K chunk) into one of two TMEM accumulators (128
 // columns each) while warps 0-7 drain the other: each thread owns one row and 64 columns,
